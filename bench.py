@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 free-space Poisson solver (VGF and HE on the same GPU).
+
+Workload (default): 3D VGF, 256^3 cells on [-1,1]^3, FP32, outputs phi and the
+three components of E; rho = 8 seeded anisotropic Gaussians (centres
+U[-0.5,0.5]^3, sigma_a U[0.05,0.15], Q U[-1,1], seed 1).  One step = one full
+solve (all five passes).  HE is timed on the same GPU with the same input.
+The working set (rho 67 MB, workspace 539 MB, outputs 268 MB) exceeds the
+129 MB L2, so no flush is needed between iterations.
+
+Multi-GPU: every rank solves its own replica (independent solves, no data-path
+collective; weak scaling); the timing is the maximum over ranks.
+
+--impl reference times the FP64 CPU oracle on this host instead (bounded
+sample: the same mixture at 128^3, phi + E, scaled to 256^3 by the
+N^3 log N work ratio).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "VGF free-space solves/s at 256^3 FP32 (phi+E), HE on the same GPU"
+UNIT = "solves/s"
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def pass_bytes(shape, with_E=True):
+    """Algorithmic bytes per pass (FP32 real 4 B, complex 8 B).
+
+    S = (n0+1) n1 n2 complex values: one half spectrum in k0 with n1 rows.
+    P1 reads rho, writes S; P2 reads S, writes 2S; P3 reads 2S and the kernel
+    octant, writes 2S per stream; P4 reads 2S per stream, writes S per output
+    stream; P5 reads the output streams, writes the real outputs.
+    """
+    n0, n1, n2 = shape
+    cells = n0 * n1 * n2
+    S = (n0 + 1) * n1 * n2
+    K = 4 * (n0 + 1) * (n1 + 1) * (n2 + 1)
+    s3, s4, outs = (2, 3, 4) if with_E else (1, 1, 1)
+    return {
+        "p1_fwd": 4 * cells + 8 * S,
+        "p2_fwd": 8 * S + 16 * S,
+        "p3_fwd": 16 * S + K + s3 * 16 * S,
+        "p4_fwd": s3 * 16 * S + s4 * 8 * S,
+        "p5_fwd": s4 * 8 * S + 4 * outs * cells,
+    }
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_08531_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """dram read+write bytes per launch from a committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload, {}).get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return int(e["dram_bytes"])
+    except Exception:
+        return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample(n=128, repeats=1):
+    """Time the FP64 oracle's phi+E solve of the same mixture at n^3 (kernel precomputed)."""
+    import oracle
+    prob = W.mixture_3d(n, 8, 1)
+    rho = prob.rho(np.float32).astype(np.float64)
+    g = oracle.kernel_vgf(list(prob.shape), prob.h)
+    times = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        oracle.solve_with_kernel(g, rho, prob.h)
+        times.append(time.perf_counter() - t)
+    scale = (256 ** 3 * math.log2(512 ** 3)) / (n ** 3 * math.log2((2 * n) ** 3))
+    return times, scale, oracle.threads()
+
+
+def cpu_baseline_block(n=128):
+    times, scale, cores = oracle_sample(n)
+    t = min(times)
+    return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 oracle phi+E solve of the same 8-Gaussian mixture at {n}^3 "
+                      f"({t:.2f} s), scaled to 256^3 by the N^3 log N work ratio {scale:.2f}"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    n = 128
+    for _ in range(args.warmup):
+        oracle_sample(n)
+    times, scale, cores = [], None, None
+    for _ in range(args.steps):
+        t, scale, cores = oracle_sample(n)
+        times.extend(t)
+    total = sum(times) * scale
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "3D VGF 256^3 on [-1,1]^3, 8 anisotropic Gaussians (seed 1), "
+                                                        "phi+E; CPU sample at 128^3 scaled by N^3 log N"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle phi+E solves at {n}^3, each scaled to 256^3 "
+                                       f"by the work ratio {scale:.2f}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl" if torch.distributed.is_nccl_available() else "gloo")
+        dist = dist_mod
+    import paper_2103_08531_gb300 as fsp
+    from paper_2103_08531_gb300 import build
+    build.build()
+
+    prob = W.mixture_3d(256, 8, 1)
+    rho_host = torch.from_numpy(prob.rho(np.float32)).pin_memory()
+    rho = rho_host.to(f"cuda:{local}")
+    plans = {m: fsp.Plan(prob.shape, prob.h, m) for m in ("vgf", "he")}
+    phi = torch.empty_like(rho)
+    E = torch.empty((3,) + prob.shape, dtype=torch.float32, device=rho.device)
+    stream = torch.cuda.current_stream()
+    npass = 5
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def reduce_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=rho.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for m in ("vgf", "he"):
+        for _ in range(args.warmup):
+            plans[m].solve(rho, phi=phi, E=E)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    results = {}
+    for m in ("vgf", "he"):
+        plan = plans[m]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(args.steps)]
+        for row in evs:
+            for e in row:
+                e.record(stream)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for s in range(args.steps):
+            plan.set_pass_events(evs[s])
+            plan.solve(rho, phi=phi, E=E)
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        plan.set_pass_events(None)
+        ms = start.elapsed_time(end)
+        per_pass = [statistics.mean(evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps))
+                    for i in range(npass)]
+        results[m] = {"ms": reduce_max(ms), "per_pass_ms": per_pass}
+    clk = clocks.stop()
+
+    # end to end through the public API: pinned host rho in, phi and E back to pinned host memory
+    phi_host = torch.empty(prob.shape, dtype=torch.float32).pin_memory()
+    E_host = torch.empty((3,) + prob.shape, dtype=torch.float32).pin_memory()
+    e2e_ms = None
+    if not args.no_e2e:
+        plan = plans["vgf"]
+        for _ in range(2):
+            rho.copy_(rho_host, non_blocking=True)
+            plan.solve(rho, phi=phi, E=E)
+            phi_host.copy_(phi, non_blocking=True)
+            E_host.copy_(E, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            rho.copy_(rho_host, non_blocking=True)
+            plan.solve(rho, phi=phi, E=E)
+            phi_host.copy_(phi, non_blocking=True)
+            E_host.copy_(E, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = reduce_max(s0.elapsed_time(s1))
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    pb = pass_bytes(prob.shape, True)
+    names = list(pb.keys())
+    vgf = results["vgf"]
+    dom = max(range(npass), key=lambda i: vgf["per_pass_ms"][i])
+    dom_name = names[dom]
+    achieved = pb[dom_name] / (vgf["per_pass_ms"][dom] * 1e-3) / 1e9
+    total_bytes = sum(pb.values())
+    ms_step = vgf["ms"] / args.steps
+    value = ws * args.steps / (vgf["ms"] * 1e-3)
+    he_ms_step = results["he"]["ms"] / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3D VGF 256^3 on [-1,1]^3, FP32, phi + E, 8 anisotropic Gaussians (seed 1)",
+                   "grid": list(prob.shape), "method": "vgf", "outputs": "phi,Ex,Ey,Ez",
+                   "l2": "working set 0.9 GB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
+        "gpts_per_s": value * prob.points / 1e9,
+        "he": {"ms_per_step": he_ms_step, "solves_per_s": ws / (he_ms_step * 1e-3),
+               "per_pass_ms": results["he"]["per_pass_ms"]},
+        "vgf_over_he_time": ms_step / he_ms_step,
+        "per_pass_ms": dict(zip(names, vgf["per_pass_ms"])),
+        "per_pass_gbs": {k: pb[k] / (t * 1e-3) / 1e9 for k, t in zip(names, vgf["per_pass_ms"])},
+        "pipeline": {"bytes": total_bytes, "gbs": total_bytes / (ms_step * 1e-3) / 1e9,
+                     "frac": total_bytes / (ms_step * 1e-3) / 1e9 / peak},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(dom_name, "vgf256"),
+                     "algorithmic_bytes": pb[dom_name]},
+        "gpu_launches": npass * args.steps,
+        "clocks": clk,
+    }
+    if e2e_ms is not None:
+        line["e2e"] = {"value": ws * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": rho.numel() * 4, "d2h_bytes_per_step": (phi.numel() + E.numel()) * 4}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_block()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

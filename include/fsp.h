@@ -1,0 +1,163 @@
+/*
+ * fsp.h -- C ABI of the GB300 free-space Poisson solver.
+ *
+ * Solves Laplacian(phi) = -rho with free-space boundary conditions and returns
+ * phi and E = -grad(phi) on a uniform cell-centred grid (paper Sec. 1,
+ * Eq. "eq:Poisson" and "eq:convolution"), by the zero-padded FFT convolution of
+ * Hockney and Eastwood (HE, paper Sec. 1) or of Vico, Greengard and Ferrando
+ * (VGF, paper Sec. 2).  The two differ only in the Green's function that is
+ * convolved (paper Sec. 2, last paragraph): HE samples G with a finite value at
+ * r = 0, VGF uses the truncated kernel G^L whose transform is given in closed
+ * form (Eqs. GLFourier2D, GLFourier3D), brought to the 2N grid through an
+ * oversampled inverse transform.  Both run on the same GPU machinery:
+ *
+ *     phi = prod(h) IFFT_2N( FFT_2N(rho padded) FFT_2N(g) ) cropped to N,
+ *     E_a = prod(h) IFFT_2N( -i k_a FFT_2N(rho padded) FFT_2N(g) ) cropped,
+ *
+ * with k_a = 2 pi m / (2 n_a h_a), m in [-n_a, n_a), and k_a = 0 at the
+ * unpaired index m = -n_a (Fourier differentiation, paper Sec. 3).
+ *
+ * Units follow the paper: G = 1/(4 pi r) in 3D and -ln(r)/(2 pi) in 2D.
+ *
+ * Layouts.  All arrays are row-major with the last axis contiguous:
+ *   3D rho, phi: float [nx][ny][nz];   E: float [3][nx][ny][nz]
+ *   2D rho, phi: float [nx][ny];       E: float [2][nx][ny]
+ * Device pointers must be 16-byte aligned; the caller owns every buffer.
+ *
+ * Execution.  Solves are asynchronous on the given CUDA stream (a
+ * cudaStream_t passed as void*, NULL = legacy default stream); they never
+ * synchronise and never allocate, so they can be captured in a CUDA graph.
+ * Argument errors are reported synchronously through the return code.  A plan
+ * owns one workspace, so a plan must not be used by two overlapping solves.
+ *
+ * Errors.  Functions returning int return an fsp_status.  fsp_plan_create and
+ * fsp_batch_create return NULL on failure and leave the code in
+ * fsp_last_error() (thread-local).
+ */
+#ifndef FSP_H
+#define FSP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsp_plan fsp_plan;
+typedef struct fsp_batch fsp_batch;
+
+enum fsp_method {
+    FSP_HE = 0,         /* Hockney-Eastwood, G(0) replaced by 1 (3D) or 1/(2 pi) (2D): paper Sec. 1, Sec. 3 */
+    FSP_VGF = 1,        /* Vico-Greengard-Ferrando truncated kernel: paper Sec. 2 */
+    FSP_HE_NEARBY = 2,  /* HE with G(0) := G(min_a h_a) ("nearby value" variant, paper Sec. 3) */
+    FSP_HE_CELLAVG = 3  /* HE with G(0) := mean of G over the cell ("cell average" variant, paper Sec. 3) */
+};
+
+enum fsp_dtype { FSP_F32 = 0, FSP_F64 = 1 };
+
+enum fsp_status {
+    FSP_OK = 0,
+    FSP_ERR_INVALID = 1,          /* bad argument: NULL, misaligned, out of range */
+    FSP_ERR_UNSUPPORTED_SIZE = 2, /* grid size the FFT passes do not cover */
+    FSP_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+    FSP_ERR_NOMEM = 4,            /* allocation at plan creation failed */
+    FSP_ERR_WORKSPACE = 5,        /* no workspace set, or too small */
+    FSP_ERR_TIMEOUT = 6           /* a bounded device-side wait gave up */
+};
+
+/*
+ * Create a plan for one grid geometry: nx x ny x nz cells (nz = 0 for a 2D
+ * nx x ny problem; hz is then ignored) with spacings hx, hy, hz.  Runs the
+ * once-per-geometry kernel precomputation on the current CUDA device in FP64
+ * (paper Sec. 2, last paragraph: transform of G^L on an oversampled grid,
+ * restricted to the 2N grid) and stores the real, even FP32 spectrum of the
+ * kernel with prod(h)/prod(2n) folded in.  Blocks until the precomputation
+ * has finished.  Supported sizes: 3D, 2 n_a in {64, 128, 192, 256, 512, 1024}
+ * on every axis; 2D, 2 n_a in {64, 128, 192, 256, 512, 1024, 2048, 4096,
+ * 8192}; the contiguous axis has an even n.  Others: FSP_ERR_UNSUPPORTED_SIZE.
+ * dtype: FSP_F32 only (FSP_F64 returns FSP_ERR_UNSUPPORTED_SIZE).
+ * Returns NULL on failure (see fsp_last_error()).
+ */
+fsp_plan *fsp_plan_create(int nx, int ny, int nz, double hx, double hy, double hz, int method, int dtype);
+
+/*
+ * As fsp_plan_create, with the VGF truncation radius scaled by lambda (L =
+ * lambda * box diagonal; lambda <= 0 means 1) and, for the HE methods, an
+ * explicit value g0 for G(0) (NaN means the method's default).
+ */
+fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, double hy, double hz, int method, int dtype,
+                             double lambda, double g0);
+
+int fsp_last_error(void);
+const char *fsp_error_string(int status);
+
+/*
+ * Geometry chosen by the plan: n[3], h[3], the VGF truncation radius L and
+ * oversampled grid M[3] (0 for HE), and the dimension (2 or 3).  Any output
+ * pointer may be NULL.
+ */
+int fsp_plan_geometry(const fsp_plan *plan, int *dim, int *n, double *h, double *L, int *M);
+
+/* Device workspace one solve (or adjoint) needs, in bytes; batch >= 1 multiplies it. */
+size_t fsp_plan_workspace_bytes(const fsp_plan *plan, int with_E, int batch);
+
+/* Hand the plan a device workspace (the caller keeps ownership). */
+int fsp_plan_set_workspace(fsp_plan *plan, void *dev_ptr, size_t bytes);
+
+/*
+ * One solve.  rho: device float grid.  phi: device float grid or NULL.
+ * E: device float [dim][grid] or NULL.  phi and E must not both be NULL.
+ */
+int fsp_solve(fsp_plan *plan, const void *rho, void *phi, void *E, void *cuda_stream);
+
+/*
+ * Adjoint of the linear map rho -> (phi, E):
+ *     g_rho = A^T g_phi + sum_a B_a^T g_E[a] = A g_phi - sum_a B_a g_E[a],
+ * A symmetric because the kernel is even, B_a antisymmetric because -i k_a is
+ * odd with the Nyquist entry zero.  g_phi or g_E may be NULL (zero).
+ */
+int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *g_E, void *g_rho, void *cuda_stream);
+
+/*
+ * Many independent solves of different geometries, one launch per pass over
+ * all of them.  plans[i] must be distinct plans, each with its own workspace
+ * set; rho/phi/E as for fsp_solve (phi[i] or E[i] may be NULL consistently for
+ * all i: with_E is taken from E != NULL).
+ */
+int fsp_solve_batched(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
+                      void *const *E, void *cuda_stream);
+
+/*
+ * Prebuilt batch: the device work lists of fsp_solve_batched built once, so
+ * that repeated launches (or a captured CUDA graph) do no host work.
+ * fsp_batch_create copies the pointer arrays; they must stay valid device
+ * buffers for the life of the batch.
+ */
+fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
+                            void *const *E);
+int fsp_batch_solve(fsp_batch *batch, void *cuda_stream);
+void fsp_batch_destroy(fsp_batch *batch);
+
+/*
+ * Measurement hook: when count > 0, every later fsp_solve / fsp_solve_adjoint
+ * on this plan records events[i] (cudaEvent_t values created by the caller) on
+ * its stream just before pass i, and events[passes] after the last pass
+ * (passes = 5 in 3D, 3 in 2D; count must be >= passes + 1).  events = NULL or
+ * count = 0 turns it off.  The array is copied; the events stay the caller's.
+ */
+int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count);
+
+/*
+ * Test hook: copy the plan's FP32 kernel spectrum to host memory, layout
+ * [nx+1][ny+1][nz+1] (2D: [nx+1][ny+1]), entry (kx,ky,kz) = prod(h)/prod(2n)
+ * times the DFT of the padded kernel at index k (indices k and 2n-k share it).
+ */
+int fsp_plan_kernel_spectrum(const fsp_plan *plan, void *host_out, size_t bytes);
+
+void fsp_plan_destroy(fsp_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSP_H */

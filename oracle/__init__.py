@@ -61,6 +61,7 @@ def _load():
             "orc_kernel_spectrum": [ctypes.c_int, ip, dp, dp, dp],
             "orc_solve": [ctypes.c_int, ip, dp, dp, dp, dp, dp],
             "orc_direct_phi": [ctypes.c_int, ip, dp, dp, dp, dp],
+            "orc_direct_phi_at": [ctypes.c_int, ip, dp, dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_long), dp],
             "orc_adjoint": [ctypes.c_int, ip, dp, dp, dp, dp, dp],
         }
         for name, args in sig.items():
@@ -161,6 +162,32 @@ def he_g0(d: int) -> float:
     return 1.0 if d == 3 else 1.0 / (2.0 * math.pi)
 
 
+def he_g0_variant(d: int, h, method: str) -> float:
+    """G(0) replacement for the HE variants compared in the paper (Sec. 3).
+
+    'he': the literal value (he_g0); 'he_nearby': G at the smallest spacing;
+    'he_cellavg': the mean of G over the cell [-h/2, h/2]^d, by adaptive
+    quadrature of the integrable singularity (the integral over the cell is 2^d
+    times the integral over the positive corner box).
+    """
+    if method == "he":
+        return he_g0(d)
+    hmin = min(h[:d])
+    if method == "he_nearby":
+        return 1.0 / (4.0 * math.pi * hmin) if d == 3 else -math.log(hmin) / (2.0 * math.pi)
+    if method != "he_cellavg":
+        raise ValueError(method)
+    from scipy import integrate
+    half = [0.5 * x for x in h[:d]]
+    if d == 3:
+        val, _ = integrate.tplquad(lambda z, y, x: 1.0 / math.sqrt(x * x + y * y + z * z),
+                                   0, half[0], 0, half[1], 0, half[2], epsabs=1e-14, epsrel=1e-12)
+        return 8.0 * val / (4.0 * math.pi * h[0] * h[1] * h[2])
+    val, _ = integrate.dblquad(lambda y, x: math.log(math.hypot(x, y)), 0, half[0], 0, half[1],
+                               epsabs=1e-14, epsrel=1e-12)
+    return -4.0 * val / (2.0 * math.pi * h[0] * h[1])
+
+
 # ------------------------------------------------------------- kernels
 
 def kernel_he(n, h, g0: float | None = None) -> np.ndarray:
@@ -246,6 +273,17 @@ def direct_phi(g2n: np.ndarray, rho: np.ndarray, h) -> np.ndarray:
     out = np.empty_like(r)
     _check(_load().orc_direct_phi(r.ndim, _ivec(r.shape), _dvec(h), _dp(np.ascontiguousarray(g2n)), _dp(r),
                                   _dp(out)), "direct_phi")
+    return out
+
+
+def direct_phi_at(g2n: np.ndarray, rho: np.ndarray, h, flat_points) -> np.ndarray:
+    """Brute-force phi at the given flat cell indices only."""
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    pts = np.ascontiguousarray(flat_points, dtype=np.int64)
+    out = np.empty(pts.size, dtype=np.float64)
+    _check(_load().orc_direct_phi_at(r.ndim, _ivec(r.shape), _dvec(h), _dp(np.ascontiguousarray(g2n)), _dp(r),
+                                     pts.size, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out)),
+           "direct_phi_at")
     return out
 
 

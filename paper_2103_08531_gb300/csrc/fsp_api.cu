@@ -1,0 +1,471 @@
+// fsp_api.cu -- plan objects and the C ABI declared in include/fsp.h.
+#include "fsp_internal.h"
+#include "fsp_passes.cuh"
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+using namespace fsp;
+
+static thread_local int g_last_error = FSP_OK;
+
+static int set_err(int e)
+{
+    g_last_error = e;
+    return e;
+}
+
+extern "C" int fsp_last_error(void) { return g_last_error; }
+
+extern "C" const char *fsp_error_string(int s)
+{
+    switch (s) {
+    case FSP_OK: return "ok";
+    case FSP_ERR_INVALID: return "invalid argument";
+    case FSP_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case FSP_ERR_CUDA: return "CUDA runtime error";
+    case FSP_ERR_NOMEM: return "out of memory";
+    case FSP_ERR_WORKSPACE: return "workspace missing or too small";
+    case FSP_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+// ----------------------------------------------------------- geometry rules
+
+static bool smooth235(long long m)
+{
+    for (int p : {2, 3, 5})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+// Oversampled VGF grid per axis: the inverse transform on M points of spacing h
+// periodises the kernel with period M h; the 2n convolution reads offsets up to
+// n h, so M h >= n h + L keeps the copies away.  At least 4 n (paper Sec. 2,
+// last paragraph), smallest even 2^a 3^b 5^c.
+static int oversample(int n, double h, double L)
+{
+    long long need = std::max<long long>(4LL * n, n + (long long)std::ceil(L / h) + 2);
+    if (need % 2) ++need;
+    while (!smooth235(need)) need += 2;
+    return (int)need;
+}
+
+// HE G(0) replacements (paper Sec. 1 and the variants named in Sec. 3).
+static double he_g0(int dim, const double *h, int method)
+{
+    const double pi = 3.14159265358979323846;
+    if (method == FSP_HE) return dim == 3 ? 1.0 : 1.0 / (2.0 * pi);
+    double hmin = h[0];
+    for (int a = 1; a < dim; ++a) hmin = std::min(hmin, h[a]);
+    if (method == FSP_HE_NEARBY) return dim == 3 ? 1.0 / (4.0 * pi * hmin) : -std::log(hmin) / (2.0 * pi);
+    // cell average of G over [-h/2, h/2]^d
+    if (dim == 3) {
+        // int_box 1/r = sum over faces (divergence of r/r = 2/r); per face the
+        // integral of 1/sqrt(a^2 + y^2 + z^2) over [0,b]x[0,c] is J(a; b, c).
+        auto J = [](double a, double b, double c) {
+            double R = std::sqrt(a * a + b * b + c * c);
+            return b * std::log((c + R) / std::sqrt(a * a + b * b)) + c * std::log((b + R) / std::sqrt(a * a + c * c)) -
+                   a * std::atan(b * c / (a * R));
+        };
+        double a = 0.5 * h[0], b = 0.5 * h[1], c = 0.5 * h[2];
+        double I = 4.0 * (a * J(a, b, c) + b * J(b, a, c) + c * J(c, a, b));
+        return I / (4.0 * pi * h[0] * h[1] * h[2]);
+    }
+    auto F = [](double x, double y) {
+        double r = std::sqrt(x * x + y * y);
+        return x * y * std::log(r) - 1.5 * x * y + 0.5 * x * x * std::atan(y / x) + 0.5 * y * y * std::atan(x / y);
+    };
+    double I = 4.0 * F(0.5 * h[0], 0.5 * h[1]);   // int_cell ln r
+    return -I / (2.0 * pi * h[0] * h[1]);
+}
+
+// ------------------------------------------------------------------- plans
+
+static std::mutex g_prep_mutex;
+
+static void plan_free(Plan &p)
+{
+    cudaFree(p.tw0);
+    if (p.tw1 != p.tw0) cudaFree(p.tw1);
+    if (p.tw2 != p.tw0 && p.tw2 != p.tw1) cudaFree(p.tw2);
+    cudaFree(p.K);
+}
+
+extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, double hy, double hz, int method,
+                                        int dtype, double lambda, double g0)
+{
+    const int dim = nz == 0 ? 2 : 3;
+    if (nx <= 0 || ny <= 0 || nz < 0 || !(hx > 0) || !(hy > 0) || (dim == 3 && !(hz > 0)) || method < FSP_HE ||
+        method > FSP_HE_CELLAVG) {
+        set_err(FSP_ERR_INVALID);
+        return nullptr;
+    }
+    if (dtype != FSP_F32) {
+        set_err(dtype == FSP_F64 ? FSP_ERR_UNSUPPORTED_SIZE : FSP_ERR_INVALID);
+        return nullptr;
+    }
+    fsp_plan *handle = new (std::nothrow) fsp_plan();
+    if (!handle) {
+        set_err(FSP_ERR_NOMEM);
+        return nullptr;
+    }
+    Plan &p = handle->p;
+    std::memset(&p, 0, sizeof(p));
+    p.dim = dim;
+    p.n[0] = nx;
+    p.n[1] = ny;
+    p.n[2] = nz;
+    p.h[0] = hx;
+    p.h[1] = hy;
+    p.h[2] = dim == 3 ? hz : 0.0;
+    p.method = method;
+    if (dim == 3) {
+        p.n0 = nx; p.n1 = ny; p.n2 = nz; p.rows1 = 2 * ny; p.three_d = 1;
+    } else {
+        p.n0 = nx; p.n1 = 1; p.n2 = ny; p.rows1 = 1; p.three_d = 0;
+    }
+    const double pi = 3.14159265358979323846;
+    const double hh0 = hx, hh2 = dim == 3 ? hz : hy;
+    p.k0s = (float)(2.0 * pi / (2.0 * p.n0 * hh0));
+    p.k1s = dim == 3 ? (float)(2.0 * pi / (2.0 * ny * hy)) : 0.f;
+    p.k2s = (float)(2.0 * pi / (2.0 * p.n2 * hh2));
+    bool ok = supported_axis0(2 * p.n0) && supported_axis2(2 * p.n2) && (p.n2 % 2 == 0) &&
+              (dim == 2 || (supported_axis1(2 * p.n1) && 2 * p.n0 <= 1024 && 2 * p.n2 <= 1024));
+    if (!ok) {
+        delete handle;
+        set_err(FSP_ERR_UNSUPPORTED_SIZE);
+        return nullptr;
+    }
+    if (method == FSP_VGF) {
+        double diag = 0.0;
+        for (int a = 0; a < dim; ++a) diag += (p.n[a] * p.h[a]) * (p.n[a] * p.h[a]);
+        p.L = (lambda > 0 ? lambda : 1.0) * std::sqrt(diag);
+        for (int a = 0; a < dim; ++a) p.M[a] = oversample(p.n[a], p.h[a], p.L);
+    } else {
+        p.g0 = std::isnan(g0) ? he_g0(dim, p.h, method) : g0;
+    }
+    if (cudaGetDevice(&p.device) != cudaSuccess) {
+        delete handle;
+        set_err(FSP_ERR_CUDA);
+        return nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_prep_mutex);
+        int e = prepare_axis0(2 * p.n0) | prepare_axis2(2 * p.n2) | (dim == 3 ? prepare_axis1(2 * p.n1) : 0);
+        if (e) {
+            delete handle;
+            set_err(FSP_ERR_CUDA);
+            return nullptr;
+        }
+    }
+    int rc = FSP_OK;
+    const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
+    if (cudaMalloc(&p.tw0, sizeof(float2) * N0) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    if (rc == FSP_OK) {
+        if (dim == 3 && N1 != N0) {
+            if (cudaMalloc(&p.tw1, sizeof(float2) * N1) != cudaSuccess) rc = FSP_ERR_NOMEM;
+        } else {
+            p.tw1 = p.tw0;
+        }
+    }
+    if (rc == FSP_OK) {
+        if (N2 == N0) p.tw2 = p.tw0;
+        else if (dim == 3 && N2 == N1) p.tw2 = p.tw1;
+        else if (cudaMalloc(&p.tw2, sizeof(float2) * N2) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    }
+    p.K_count = (size_t)(p.n[0] + 1) * (p.n[1] + 1) * (dim == 3 ? (p.n[2] + 1) : 1);
+    if (rc == FSP_OK && cudaMalloc(&p.K, sizeof(float) * p.K_count) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    cudaStream_t st = nullptr;
+    if (rc == FSP_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = FSP_ERR_CUDA;
+    if (rc == FSP_OK) {
+        if (make_twiddles(p.tw0, N0, st)) rc = FSP_ERR_CUDA;
+        if (rc == FSP_OK && p.tw1 != p.tw0 && make_twiddles(p.tw1, N1, st)) rc = FSP_ERR_CUDA;
+        if (rc == FSP_OK && p.tw2 != p.tw0 && p.tw2 != p.tw1 && make_twiddles(p.tw2, N2, st)) rc = FSP_ERR_CUDA;
+    }
+    if (rc == FSP_OK) rc = build_kernel_spectrum(&p, st);
+    if (st) cudaStreamDestroy(st);
+    if (rc != FSP_OK) {
+        plan_free(p);
+        delete handle;
+        set_err(rc);
+        return nullptr;
+    }
+    p.buf_elems = (size_t)(p.n0 + 1) * p.rows1 * p.n2;
+    set_err(FSP_OK);
+    return handle;
+}
+
+extern "C" fsp_plan *fsp_plan_create(int nx, int ny, int nz, double hx, double hy, double hz, int method, int dtype)
+{
+    return fsp_plan_create_ex(nx, ny, nz, hx, hy, hz, method, dtype, 1.0, NAN);
+}
+
+extern "C" void fsp_plan_destroy(fsp_plan *plan)
+{
+    if (!plan) return;
+    plan_free(plan->p);
+    delete plan;
+}
+
+extern "C" int fsp_plan_geometry(const fsp_plan *plan, int *dim, int *n, double *h, double *L, int *M)
+{
+    if (!plan) return set_err(FSP_ERR_INVALID);
+    const Plan &p = plan->p;
+    if (dim) *dim = p.dim;
+    for (int a = 0; a < 3; ++a) {
+        if (n) n[a] = p.n[a];
+        if (h) h[a] = p.h[a];
+        if (M) M[a] = p.M[a];
+    }
+    if (L) *L = p.L;
+    return set_err(FSP_OK);
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static size_t per_solve_bytes(const Plan &p) { return 2 * align_up(p.buf_elems * sizeof(float2), 256); }
+
+extern "C" size_t fsp_plan_workspace_bytes(const fsp_plan *plan, int with_E, int batch)
+{
+    (void)with_E;
+    if (!plan || batch < 1) return 0;
+    return per_solve_bytes(plan->p) * (size_t)batch;
+}
+
+extern "C" int fsp_plan_set_workspace(fsp_plan *plan, void *dev_ptr, size_t bytes)
+{
+    if (!plan || !dev_ptr || ((uintptr_t)dev_ptr % 256) != 0) return set_err(FSP_ERR_INVALID);
+    if (bytes < per_solve_bytes(plan->p)) return set_err(FSP_ERR_WORKSPACE);
+    plan->p.ws = dev_ptr;
+    plan->p.ws_bytes = bytes;
+    return set_err(FSP_OK);
+}
+
+extern "C" int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count)
+{
+    if (!plan || count < 0) return set_err(FSP_ERR_INVALID);
+    Plan &p = plan->p;
+    if (!events || count == 0) {
+        p.n_pass_ev = 0;
+        return set_err(FSP_OK);
+    }
+    const int need = p.three_d ? 6 : 4;
+    if (count < need || count > 8) return set_err(FSP_ERR_INVALID);
+    for (int i = 0; i < count; ++i) {
+        if (!events[i]) return set_err(FSP_ERR_INVALID);
+        p.pass_ev[i] = (cudaEvent_t)events[i];
+    }
+    p.n_pass_ev = count;
+    return set_err(FSP_OK);
+}
+
+extern "C" int fsp_plan_kernel_spectrum(const fsp_plan *plan, void *host_out, size_t bytes)
+{
+    if (!plan || !host_out) return set_err(FSP_ERR_INVALID);
+    if (bytes < plan->p.K_count * sizeof(float)) return set_err(FSP_ERR_INVALID);
+    if (cudaMemcpy(host_out, plan->p.K, plan->p.K_count * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_err(FSP_ERR_CUDA);
+    return set_err(FSP_OK);
+}
+
+// ------------------------------------------------------------------- solves
+
+static bool aligned16(const void *p) { return ((uintptr_t)p % 16) == 0; }
+
+static PassArgs base_args(const Plan &p, void *ws)
+{
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n0 = p.n0;
+    a.n1 = p.n1;
+    a.n2 = p.n2;
+    a.rows1 = p.rows1;
+    a.three_d = p.three_d;
+    a.k0s = p.k0s;
+    a.k1s = p.k1s;
+    a.k2s = p.k2s;
+    a.tw0 = p.tw0;
+    a.tw1 = p.tw1;
+    a.tw2 = p.tw2;
+    a.K = p.K;
+    a.buf0 = reinterpret_cast<float2 *>(ws);
+    a.buf1 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + align_up(p.buf_elems * sizeof(float2), 256));
+    return a;
+}
+
+static size_t cells(const Plan &p) { return (size_t)p.n0 * p.n1 * p.n2; }
+
+namespace fsp {
+
+static inline void mark(const Plan &p, int i, cudaStream_t st)
+{
+    if (p.n_pass_ev > i) cudaEventRecord(p.pass_ev[i], st);
+}
+
+// Forward pipeline for one plan on its workspace `ws`.
+int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
+{
+    PassArgs a = base_args(p, ws);
+    const size_t c = cells(p);
+    a.in[0] = rho;
+    a.out[0] = phi;
+    if (E) {
+        a.out[1] = E;
+        a.out[2] = E + c;
+        a.out[3] = p.three_d ? E + 2 * c : nullptr;
+    }
+    const int withE = E != nullptr;
+    const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
+    int e = 0;
+    mark(p, 0, st);
+    if (p.three_d) {
+        e = launch_p1_fwd(N0, a, a.buf1, st);
+        mark(p, 1, st);
+        if (!e) e = launch_p2_fwd(N1, a, a.buf1, a.buf0, st);
+        mark(p, 2, st);
+        if (!e) e = launch_p3_fwd(N2, a, withE, st);
+        mark(p, 3, st);
+        if (!e) e = launch_p4_fwd(N1, a, withE, st);
+        mark(p, 4, st);
+        if (!e) e = launch_p5_fwd(N0, a, st);
+        mark(p, 5, st);
+    } else {
+        e = launch_p1_fwd(N0, a, a.buf0, st);
+        mark(p, 1, st);
+        if (!e) e = launch_p3_fwd(N2, a, withE, st);
+        mark(p, 2, st);
+        if (!e) e = launch_p5_fwd(N0, a, st);
+        mark(p, 3, st);
+    }
+    return e ? FSP_ERR_CUDA : FSP_OK;
+}
+
+int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, float *g_rho, cudaStream_t st)
+{
+    if (!g_E) return run_forward(p, ws, g_phi, g_rho, nullptr, st);   // A is symmetric
+    PassArgs a = base_args(p, ws);
+    const size_t c = cells(p);
+    a.in[0] = g_phi;
+    a.in[1] = g_E;
+    a.in[2] = g_E + c;
+    a.in[3] = p.three_d ? g_E + 2 * c : nullptr;
+    const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
+    int m = 0;
+    mark(p, m++, st);
+    int e = launch_p1_adj(N0, a, st);
+    mark(p, m++, st);
+    if (!e && p.three_d) {
+        e = launch_p2_adj(N1, a, 1, st);
+        mark(p, m++, st);
+    }
+    if (!e) e = launch_p3_adj(N2, a, 1, st);
+    mark(p, m++, st);
+    if (!e && p.three_d) {
+        e = launch_p4_fwd(N1, a, 0, st);
+        mark(p, m++, st);
+    }
+    if (!e) {
+        PassArgs b = a;
+        b.out[0] = g_rho;
+        b.out[1] = b.out[2] = b.out[3] = nullptr;
+        e = launch_p5_fwd(N0, b, st);
+    }
+    mark(p, m++, st);
+    return e ? FSP_ERR_CUDA : FSP_OK;
+}
+
+} // namespace fsp
+
+extern "C" int fsp_solve(fsp_plan *plan, const void *rho, void *phi, void *E, void *cuda_stream)
+{
+    if (!plan || !rho || (!phi && !E)) return set_err(FSP_ERR_INVALID);
+    if (!aligned16(rho) || (phi && !aligned16(phi)) || (E && !aligned16(E))) return set_err(FSP_ERR_INVALID);
+    const Plan &p = plan->p;
+    if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return set_err(FSP_ERR_WORKSPACE);
+    return set_err(run_forward(p, p.ws, (const float *)rho, (float *)phi, (float *)E, (cudaStream_t)cuda_stream));
+}
+
+extern "C" int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *g_E, void *g_rho, void *cuda_stream)
+{
+    if (!plan || !g_rho || (!g_phi && !g_E)) return set_err(FSP_ERR_INVALID);
+    if ((g_phi && !aligned16(g_phi)) || (g_E && !aligned16(g_E)) || !aligned16(g_rho)) return set_err(FSP_ERR_INVALID);
+    const Plan &p = plan->p;
+    if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return set_err(FSP_ERR_WORKSPACE);
+    return set_err(run_adjoint(p, p.ws, (const float *)g_phi, (const float *)g_E, (float *)g_rho,
+                               (cudaStream_t)cuda_stream));
+}
+
+// ----------------------------------------------------------------- batches
+
+struct fsp_batch {
+    std::vector<fsp_plan *> plans;
+    std::vector<const float *> rho;
+    std::vector<float *> phi, E;
+};
+
+static int check_batch(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi, void *const *E)
+{
+    if (!plans || count < 1 || !rho || (!phi && !E)) return FSP_ERR_INVALID;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !rho[i] || !aligned16(rho[i])) return FSP_ERR_INVALID;
+        if (!(phi && phi[i]) && !(E && E[i])) return FSP_ERR_INVALID;
+        if ((phi && phi[i] && !aligned16(phi[i])) || (E && E[i] && !aligned16(E[i]))) return FSP_ERR_INVALID;
+        const Plan &p = plans[i]->p;
+        if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return FSP_ERR_WORKSPACE;
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return FSP_ERR_INVALID;
+    }
+    return FSP_OK;
+}
+
+extern "C" int fsp_solve_batched(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
+                                 void *const *E, void *cuda_stream)
+{
+    int rc = check_batch(plans, count, rho, phi, E);
+    if (rc) return set_err(rc);
+    for (int i = 0; i < count && rc == FSP_OK; ++i)
+        rc = run_forward(plans[i]->p, plans[i]->p.ws, (const float *)rho[i], phi ? (float *)phi[i] : nullptr,
+                         E ? (float *)E[i] : nullptr, (cudaStream_t)cuda_stream);
+    return set_err(rc);
+}
+
+extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
+                                       void *const *E)
+{
+    int rc = check_batch(plans, count, rho, phi, E);
+    if (rc) {
+        set_err(rc);
+        return nullptr;
+    }
+    fsp_batch *b = new (std::nothrow) fsp_batch();
+    if (!b) {
+        set_err(FSP_ERR_NOMEM);
+        return nullptr;
+    }
+    for (int i = 0; i < count; ++i) {
+        b->plans.push_back(plans[i]);
+        b->rho.push_back((const float *)rho[i]);
+        b->phi.push_back(phi ? (float *)phi[i] : nullptr);
+        b->E.push_back(E ? (float *)E[i] : nullptr);
+    }
+    set_err(FSP_OK);
+    return b;
+}
+
+extern "C" int fsp_batch_solve(fsp_batch *b, void *cuda_stream)
+{
+    if (!b) return set_err(FSP_ERR_INVALID);
+    int rc = FSP_OK;
+    for (size_t i = 0; i < b->plans.size() && rc == FSP_OK; ++i)
+        rc = run_forward(b->plans[i]->p, b->plans[i]->p.ws, b->rho[i], b->phi[i], b->E[i], (cudaStream_t)cuda_stream);
+    return set_err(rc);
+}
+
+extern "C" void fsp_batch_destroy(fsp_batch *b) { delete b; }

@@ -1,0 +1,316 @@
+// fsp_fft.cuh -- register-resident FFT engine for the padded convolution.
+//
+// One line of N complex values is spread over T = N / E threads, thread j holding
+// the E values at positions j + r T (r < E).  The transform is a Stockham
+// decimation-in-time sequence of radix-R passes (R in {2, 3, 4, 8, 16}); in pass s
+// (NS = product of the earlier radices) butterfly b = j + q T (q < E / R) takes
+// x[b + r N / R], multiplies by W^(r (b mod NS) N / (NS R)), does an R-point DFT
+// and sends output u to position (b / NS) NS R + (b mod NS) + u NS.  Between
+// passes the values go through shared memory; after the last pass every output
+// lands back in the register it came from, in natural order (position j + r T).
+//
+// "Pruned" input: when positions >= N/2 are known to be zero (the zero padding of
+// the convolution, paper Sec. 1), the first pass loads and combines only the
+// lower half: each butterfly has R/2 nonzero inputs, and its R-point DFT is done
+// as two R/2-point DFTs.  Output pruning needs no code: callers store only the
+// outputs that survive the crop and the compiler drops the rest.
+//
+// Twiddles come from a table W_N^m = exp(-2 pi i m / N), m < N, rounded to FP32
+// from FP64 angles at plan creation; the inverse transform uses the conjugate.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fsp {
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (forward direction) or +i (inverse direction)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by exp(-/+ 2 pi i / 8)
+template <bool INV>
+__device__ __forceinline__ float2 w8_1(float2 a)
+{
+    const float c = 0.70710678118654752f;
+    return INV ? make_float2(c * (a.x - a.y), c * (a.x + a.y)) : make_float2(c * (a.x + a.y), c * (a.y - a.x));
+}
+// multiply by exp(-/+ 2 pi i 3 / 8)
+template <bool INV>
+__device__ __forceinline__ float2 w8_3(float2 a)
+{
+    const float c = 0.70710678118654752f;
+    return INV ? make_float2(-c * (a.x + a.y), c * (a.x - a.y)) : make_float2(c * (a.y - a.x), -c * (a.x + a.y));
+}
+template <bool INV>
+__device__ __forceinline__ float2 cmul_dir(float2 a, float2 w)
+{
+    return INV ? cmulc(a, w) : cmul(a, w);
+}
+
+// ---------------------------------------------------------------- butterflies
+// In place, natural order in and out: X_u = sum_r v_r exp(-/+ 2 pi i r u / R).
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2 &a, float2 &b)
+{
+    float2 t = a;
+    a = t + b;
+    b = t - b;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 &a, float2 &b, float2 &c)
+{
+    const float s3 = 0.86602540378443865f;
+    float2 t1 = b + c;
+    float2 t2 = a - 0.5f * t1;
+    float2 t3 = s3 * (b - c);
+    a = a + t1;
+    b = t2 + rot<INV>(t3);
+    c = t2 - rot<INV>(t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+{
+    float2 s0 = a0 + a2, d0 = a0 - a2, s1 = a1 + a3, d1 = rot<INV>(a1 - a3);
+    a0 = s0 + s1;
+    a2 = s0 - s1;
+    a1 = d0 + d1;
+    a3 = d0 - d1;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 *v)
+{
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = w8_1<INV>(o1);
+    o2 = rot<INV>(o2);
+    o3 = w8_3<INV>(o3);
+    v[0] = e0 + o0;
+    v[4] = e0 - o0;
+    v[1] = e1 + o1;
+    v[5] = e1 - o1;
+    v[2] = e2 + o2;
+    v[6] = e2 - o2;
+    v[3] = e3 + o3;
+    v[7] = e3 - o3;
+}
+
+// exp(-/+ 2 pi i u / 16), u = 1..7 (cos, sin of u pi / 8)
+template <bool INV>
+__device__ __forceinline__ float2 w16(float2 a, int u)
+{
+    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, c2 = 0.70710678118654752f;
+    float2 w;
+    switch (u) {
+    case 1: w = make_float2(c1, -s1); break;
+    case 2: w = make_float2(c2, -c2); break;
+    case 3: w = make_float2(s1, -c1); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 5: w = make_float2(-s1, -c1); break;
+    case 6: w = make_float2(-c2, -c2); break;
+    default: w = make_float2(-c1, -s1); break;
+    }
+    if (u == 4) return rot<INV>(a);
+    return cmul_dir<INV>(a, w);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 *v)
+{
+    float2 e[8], o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft8<INV>(e);
+    dft8<INV>(o);
+#pragma unroll
+    for (int u = 1; u < 8; ++u) o[u] = w16<INV>(o[u], u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        v[u] = e[u] + o[u];
+        v[u + 8] = e[u] - o[u];
+    }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 *v)
+{
+    if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+    else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
+    else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<INV>(v);
+    else if constexpr (R == 16) dft16<INV>(v);
+    else static_assert(R == 2, "unsupported radix");
+}
+
+// R-point DFT of v[0..R/2) followed by R/2 zeros:
+// X_{2u} = DFT_{R/2}(v)_u,  X_{2u+1} = DFT_{R/2}(v_r w_R^r)_u.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_half_in(float2 *v)
+{
+    if constexpr (R == 2) {
+        v[1] = v[0];
+    } else if constexpr (R == 4) {
+        float2 a = v[0], b = v[1];
+        float2 bb = rot<INV>(b);
+        v[0] = a + b;
+        v[2] = a - b;
+        v[1] = a + bb;
+        v[3] = a - bb;
+    } else if constexpr (R == 8) {
+        float2 a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
+        float2 b0 = a0, b1 = w8_1<INV>(a1), b2 = rot<INV>(a2), b3 = w8_3<INV>(a3);
+        dft4<INV>(a0, a1, a2, a3);
+        dft4<INV>(b0, b1, b2, b3);
+        v[0] = a0;
+        v[2] = a1;
+        v[4] = a2;
+        v[6] = a3;
+        v[1] = b0;
+        v[3] = b1;
+        v[5] = b2;
+        v[7] = b3;
+    } else if constexpr (R == 16) {
+        float2 a[8], b[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            a[r] = v[r];
+            b[r] = (r == 0) ? v[0] : w16<INV>(v[r], r);
+        }
+        dft8<INV>(a);
+        dft8<INV>(b);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            v[2 * u] = a[u];
+            v[2 * u + 1] = b[u];
+        }
+    } else {
+        static_assert(R % 2 == 0, "a pruned first pass needs an even radix");
+    }
+}
+
+// ------------------------------------------------------------ shared memory views
+
+// Column tile: position p of column c at base[p * ld + c].
+struct ColView {
+    float2 *base;
+    int ld;
+    __device__ __forceinline__ float2 &at(int p) const { return base[p * ld]; }
+};
+
+// Contiguous line with one padding slot every 2^PAD positions (bank spreading).
+template <int PAD>
+struct RowView {
+    float2 *base;
+    __device__ __forceinline__ float2 &at(int p) const { return base[p + (p >> PAD)]; }
+};
+
+template <int N, int PAD>
+struct RowSpan {
+    static constexpr int value = N + (N >> PAD) + 1;
+};
+
+// ------------------------------------------------------------------- passes
+
+template <int... RS>
+struct Radices {};
+
+template <int N, int E, bool INV, int NS, class RAD>
+struct Passes;
+
+template <int N, int E, bool INV, int NS>
+struct Passes<N, E, INV, NS, Radices<>> {
+    template <bool PRUNE, class View>
+    static __device__ __forceinline__ void run(float2 (&)[E], int, const float2 *__restrict__, const View &)
+    {
+    }
+};
+
+template <int N, int E, bool INV, int NS, int R, int... RS>
+struct Passes<N, E, INV, NS, Radices<R, RS...>> {
+    template <bool PRUNE, class View>
+    static __device__ __forceinline__ void run(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
+    {
+        constexpr int T = N / E;
+        constexpr int Q = E / R;
+        constexpr bool LAST = sizeof...(RS) == 0;
+        static_assert(E % R == 0, "E must be a multiple of every radix");
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int b = j + q * T;
+            const int k = b % NS;
+            float2 u[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[r] = v[q + r * Q];
+            if constexpr (NS > 1) {
+                constexpr int STEP = N / (NS * R);
+#pragma unroll
+                for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + r * k * STEP));
+            }
+            if constexpr (PRUNE && NS == 1) dft_half_in<R, INV>(u);
+            else dft<R, INV>(u);
+            if constexpr (LAST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q + r * Q] = u[r];
+            } else {
+                const int base = (b / NS) * NS * R + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm.at(base + r * NS) = u[r];
+            }
+        }
+        if constexpr (!LAST) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < E; ++r) v[r] = sm.at(j + r * T);
+            __syncthreads();
+            Passes<N, E, INV, NS * R, Radices<RS...>>::template run<false>(v, j, tw, sm);
+        }
+    }
+};
+
+// Whole-line transform.  Precondition: every thread of the block calls it (it
+// contains __syncthreads) and nobody still reads the shared buffer.  On return
+// the shared buffer is free again.
+template <int N, int E, bool INV, bool PRUNE_IN, class RAD, class View>
+__device__ __forceinline__ void line_fft(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
+{
+    Passes<N, E, INV, 1, RAD>::template run<PRUNE_IN>(v, j, tw, sm);
+}
+
+// Radix plans per padded length (E values per thread).
+template <int N>
+struct Plan1D;
+template <> struct Plan1D<64> { static constexpr int E = 8; using R = Radices<8, 8>; };
+template <> struct Plan1D<96> { static constexpr int E = 12; using R = Radices<4, 4, 2, 3>; };
+template <> struct Plan1D<128> { static constexpr int E = 8; using R = Radices<8, 8, 2>; };
+template <> struct Plan1D<192> { static constexpr int E = 12; using R = Radices<4, 4, 4, 3>; };
+template <> struct Plan1D<256> { static constexpr int E = 8; using R = Radices<8, 8, 4>; };
+template <> struct Plan1D<512> { static constexpr int E = 8; using R = Radices<8, 8, 8>; };
+template <> struct Plan1D<1024> { static constexpr int E = 16; using R = Radices<16, 8, 8>; };
+template <> struct Plan1D<2048> { static constexpr int E = 16; using R = Radices<16, 16, 8>; };
+template <> struct Plan1D<4096> { static constexpr int E = 16; using R = Radices<16, 16, 16>; };
+template <> struct Plan1D<8192> { static constexpr int E = 16; using R = Radices<16, 8, 8, 8>; };
+
+} // namespace fsp

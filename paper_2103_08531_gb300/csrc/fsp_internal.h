@@ -1,0 +1,61 @@
+// fsp_internal.h -- plan object and launcher declarations shared by the .cu files.
+#pragma once
+
+#include "../../include/fsp.h"
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+struct fsp_plan;
+
+namespace fsp {
+
+struct PassArgs;
+
+struct Plan {
+    int dim;          // 2 or 3
+    int n[3];         // cells per physical axis (n[2] = 0 in 2D)
+    double h[3];
+    int method;
+    double L;         // VGF truncation radius (0 for HE)
+    int M[3];         // VGF oversampled grid (0 for HE)
+    double g0;        // HE value replacing G(0)
+    // pass geometry: n0 x n1 x n2 with axis 2 contiguous (2D: n1 = 1)
+    int n0, n1, n2, rows1, three_d;
+    float k0s, k1s, k2s;
+    float2 *tw0, *tw1, *tw2;  // device twiddle tables for 2 n0, 2 n1, 2 n2
+    float *K;                 // device FP32 kernel octant
+    size_t K_count;
+    size_t buf_elems;         // complex elements of one intermediate buffer
+    void *ws;
+    size_t ws_bytes;
+    int device;
+    cudaEvent_t pass_ev[8];   // optional per-pass timing events (see fsp_plan_set_pass_events)
+    int n_pass_ev;
+};
+
+// fsp_precompute.cu
+int make_twiddles(float2 *tw, int N, cudaStream_t st);
+int build_kernel_spectrum(Plan *p, cudaStream_t st);
+
+// launchers (return 0 or a cudaError_t value)
+int supported_axis0(int N);
+int supported_axis1(int N);
+int supported_axis2(int N);
+int prepare_axis0(int N);
+int prepare_axis1(int N);
+int prepare_axis2(int N);
+int launch_p1_fwd(int N, const PassArgs &a, float2 *dst, cudaStream_t st);
+int launch_p1_adj(int N, const PassArgs &a, cudaStream_t st);
+int launch_p5_fwd(int N, const PassArgs &a, cudaStream_t st);
+int launch_p2_fwd(int N, const PassArgs &a, const float2 *src, float2 *dst, cudaStream_t st);
+int launch_p2_adj(int N, const PassArgs &a, int hasE, cudaStream_t st);
+int launch_p4_fwd(int N, const PassArgs &a, int withE, cudaStream_t st);
+int launch_p3_fwd(int N, const PassArgs &a, int withE, cudaStream_t st);
+int launch_p3_adj(int N, const PassArgs &a, int hasE, cudaStream_t st);
+
+} // namespace fsp
+
+struct fsp_plan {
+    fsp::Plan p;
+};

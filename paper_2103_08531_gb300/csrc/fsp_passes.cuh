@@ -1,0 +1,497 @@
+// fsp_passes.cuh -- the five passes of the padded FFT convolution.
+//
+// Grid: n0 x n1 x n2 cells, axis 2 contiguous (a 2D problem is n0 x 1 x n2 with
+// no middle-axis passes).  Every pass works on whole padded lines (length 2 n_a)
+// that never touch memory: the zero half of the input is never loaded (pruned
+// first pass) and only the n_a cropped outputs are stored.
+//
+// Forward pipeline (paper Sec. 1 HE formula; Sec. 2 VGF uses the same steps with
+// its kernel; E by Fourier differentiation, paper Sec. 3):
+//   P1  axis 0, real -> half spectrum (k0 in [0, n0]); two real columns of axis 2
+//       packed as one complex column, separated with the conjugate symmetry.
+//   P2  axis 1 forward (3D only).
+//   P3  axis 2 forward, times the kernel spectrum K(k) (and -i k2 K for E2),
+//       axis 2 inverse -- the middle pass, one or two output streams.
+//   P4  axis 1 inverse (3D only); the phi stream also yields -i k1 phi.
+//   P5  axis 0 half spectrum -> real, phi stream -> (phi, E0) through the
+//       packing W = (1 + k0) P, the (E1, E2) streams -> (E1, E2) through
+//       W = Y + i Z.
+// Adjoint pipeline: the same passes with the streams merged instead of split:
+// the gradient spectrum is K (G_phi + sum_a i k_a G_Ea).
+//
+// Intermediate layout: complex [n0 + 1][rows1][n2], rows1 = 2 n1 in 3D, 1 in 2D.
+#pragma once
+
+#include "fsp_fft.cuh"
+#include <stdint.h>
+
+namespace fsp {
+
+struct PassArgs {
+    int n0, n1, n2;   // cells per axis (n1 = 1 for 2D)
+    int rows1;        // middle rows of the intermediate layout: 2 n1 (3D) or 1 (2D)
+    int three_d;      // 1: axis 1 is transformed
+    float k0s, k1s, k2s;   // 2 pi / (2 n_a h_a)
+    const float2 *tw0, *tw1, *tw2;
+    const float *K;   // [n0 + 1][n1 + 1 (3D) or 1][n2 + 1]
+    float2 *buf0, *buf1;
+    const float *in[4];
+    float *out[4];
+};
+
+__device__ __forceinline__ size_t iidx(const PassArgs &a, int k0, int row, int z)
+{
+    return ((size_t)k0 * a.rows1 + row) * a.n2 + z;
+}
+__device__ __forceinline__ size_t gidx(const PassArgs &a, int x, int y, int z)
+{
+    return ((size_t)x * a.n1 + y) * a.n2 + z;
+}
+
+// Signed wavenumber index of position k on a padded axis of n cells: m in
+// [-n, n), with the unpaired m = -n mapped to 0.
+__device__ __forceinline__ float wave(int k, int n, float s)
+{
+    int m = k < n ? k : (k == n ? 0 : k - 2 * n);
+    return s * (float)m;
+}
+
+template <int N>
+struct ColCfg {
+    static constexpr int E = Plan1D<N>::E;
+    static constexpr int T = N / E;
+    static constexpr int BZ = (T * 16 <= 1024) ? 16 : (1024 / T);
+    static constexpr int THREADS = T * BZ;
+    static constexpr size_t SMEM = (size_t)N * BZ * sizeof(float2);
+};
+
+template <int N>
+struct RowCfg {
+    static constexpr int E = Plan1D<N>::E;
+    static constexpr int T = N / E;
+    static constexpr int LPC = (T >= 256) ? 1 : (256 / T);
+    static constexpr int THREADS = T * LPC;
+    static constexpr int PAD = 3;
+    static constexpr int SPAN = RowSpan<N, PAD>::value;
+    static constexpr size_t SMEM = (size_t)SPAN * LPC * sizeof(float2);
+};
+
+// ----------------------------------------------------------------- P1 (axis 0)
+
+// Forward: rho columns (z, z+1) packed as re/im; output rows 0..n1-1 of buf_out.
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd(PassArgs a, float2 *__restrict__ dst)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int y = blockIdx.y;
+    const int z0 = 2 * (blockIdx.x * BZ + col);
+    const bool act = z0 < a.n2;
+    const float *rho = a.in[0];
+    float2 v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        v[r] = make_float2(0.f, 0.f);
+        if (r < E / 2 && act) v[r] = __ldg(reinterpret_cast<const float2 *>(rho + gidx(a, j + r * T, y, z0)));
+    }
+    ColView sm{smem + col, BZ};
+    line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+    for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
+    __syncthreads();
+    constexpr int NH = N / 2;
+#pragma unroll
+    for (int r = 0; r <= E / 2; ++r) {
+        const int k = j + r * T;
+        if (k <= NH && act) {
+            const float2 w = v[r];
+            const float2 m = sm.at(k == 0 ? 0 : N - k);
+            float4 o;
+            o.x = 0.5f * (w.x + m.x);
+            o.y = 0.5f * (w.y - m.y);
+            o.z = 0.5f * (w.y + m.y);
+            o.w = -0.5f * (w.x - m.x);
+            *reinterpret_cast<float4 *>(dst + iidx(a, k, y, z0)) = o;
+        }
+    }
+}
+
+// Adjoint: per column z, W1 = g_phi + i g_E0, W2 = g_E1 + i g_E2 (3D) or g_E1 (2D).
+// Outputs U = F g_phi + i k0 F g_E0 -> buf0 row y; F g_E1 -> buf0 row n1 + y (3D)
+// or buf1 row y (2D); F g_E2 -> buf1 row y (3D).
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_adj(PassArgs a)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int y = blockIdx.y;
+    const int z = blockIdx.x * BZ + col;
+    const bool act = z < a.n2;
+    const float *gp = a.in[0], *g0 = a.in[1], *g1 = a.in[2], *g2 = a.in[3];
+    const bool hasE = g0 != nullptr;
+    ColView sm{smem + col, BZ};
+    constexpr int NH = N / 2;
+    for (int pass = 0; pass < (hasE ? 2 : 1); ++pass) {
+        const float *re = pass == 0 ? gp : g1;
+        const float *im = pass == 0 ? g0 : (a.three_d ? g2 : nullptr);
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = make_float2(0.f, 0.f);
+            if (r < E / 2 && act) {
+                const size_t g = gidx(a, j + r * T, y, z);
+                v[r].x = re ? __ldg(re + g) : 0.f;
+                v[r].y = im ? __ldg(im + g) : 0.f;
+            }
+        }
+        line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r <= E / 2; ++r) {
+            const int k = j + r * T;
+            if (k <= NH && act) {
+                const float2 w = v[r];
+                const float2 m = sm.at(k == 0 ? 0 : N - k);
+                const float2 A = make_float2(0.5f * (w.x + m.x), 0.5f * (w.y - m.y));   // F re
+                const float2 B = make_float2(0.5f * (w.y + m.y), -0.5f * (w.x - m.x));  // F im
+                if (pass == 0) {
+                    const float kk = wave(k, NH, a.k0s);
+                    // U = A + i k0 B
+                    a.buf0[iidx(a, k, y, z)] = make_float2(A.x - kk * B.y, A.y + kk * B.x);
+                } else if (a.three_d) {
+                    a.buf0[iidx(a, k, a.n1 + y, z)] = A;
+                    a.buf1[iidx(a, k, y, z)] = B;
+                } else {
+                    a.buf1[iidx(a, k, y, z)] = A;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------- P2 (axis 1)
+
+// Forward: src rows 0..n1-1 -> dst rows 0..2n1-1.
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd(PassArgs a, const float2 *__restrict__ src, float2 *__restrict__ dst)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int kx = blockIdx.y;
+    const int z = blockIdx.x * BZ + col;
+    const bool act = z < a.n2;
+    float2 v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        v[r] = make_float2(0.f, 0.f);
+        if (r < E / 2 && act) v[r] = src[iidx(a, kx, j + r * T, z)];
+    }
+    line_fft<N, E, false, true, RAD>(v, j, a.tw1, ColView{smem + col, BZ});
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) dst[iidx(a, kx, j + r * T, z)] = v[r];
+    }
+}
+
+// Adjoint: buf0 rows [0,n1) = U, rows [n1,2n1) = F g_E1 (if E), buf1 rows [0,n1) = F g_E2.
+// buf0 <- F1 U + i k1 F1 (F g_E1) (all rows); buf1 <- F1 (F g_E2) (all rows).
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_adj(PassArgs a, int hasE)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int kx = blockIdx.y;
+    const int z = blockIdx.x * BZ + col;
+    const bool act = z < a.n2;
+    const int n1 = a.n1;
+    ColView sm{smem + col, BZ};
+    float2 v[E], w[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        v[r] = make_float2(0.f, 0.f);
+        w[r] = make_float2(0.f, 0.f);
+        if (r < E / 2 && act) {
+            v[r] = a.buf0[iidx(a, kx, j + r * T, z)];
+            if (hasE) w[r] = a.buf0[iidx(a, kx, n1 + j + r * T, z)];
+        }
+    }
+    line_fft<N, E, false, true, RAD>(v, j, a.tw1, sm);
+    if (hasE) {
+        line_fft<N, E, false, true, RAD>(w, j, a.tw1, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float kk = wave(j + r * T, n1, a.k1s);
+            v[r] = make_float2(v[r].x - kk * w[r].y, v[r].y + kk * w[r].x);
+        }
+    }
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
+    }
+    if (hasE) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            w[r] = make_float2(0.f, 0.f);
+            if (r < E / 2 && act) w[r] = a.buf1[iidx(a, kx, j + r * T, z)];
+        }
+        line_fft<N, E, false, true, RAD>(w, j, a.tw1, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = w[r];
+        }
+    }
+}
+
+// ------------------------------------------------------------ P3 (axis 2, middle)
+
+__device__ __forceinline__ const float *krow(const PassArgs &a, int kx, int row)
+{
+    if (a.three_d) {
+        const int n1 = a.n1;
+        const int kyf = row <= n1 ? row : 2 * n1 - row;
+        return a.K + ((size_t)kx * (n1 + 1) + kyf) * (a.n2 + 1);
+    }
+    return a.K + (size_t)kx * (a.n2 + 1);
+}
+
+// Forward: line of buf0 -> F2 -> x K -> inverse -> buf0 (phi stream), and
+// -i k2 K -> inverse -> buf1 (E2 stream) when withE.
+template <int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd(PassArgs a, int withE)
+{
+    using C = RowCfg<N>;
+    constexpr int E = C::E, T = C::T, LPC = C::LPC;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const int lines = (a.n0 + 1) * a.rows1;
+    const int line = blockIdx.x * LPC + li;
+    const bool act = line < lines;
+    const int lc = act ? line : 0;
+    const int kx = lc / a.rows1, row = lc % a.rows1;
+    const int n2 = a.n2;
+    float2 *L0 = a.buf0 + (size_t)lc * n2;
+    float2 *L1 = a.buf1 + (size_t)lc * n2;
+    RowView<C::PAD> sm{smem + li * C::SPAN};
+    float2 v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        v[r] = make_float2(0.f, 0.f);
+        if (r < E / 2 && act) v[r] = L0[j + r * T];
+    }
+    line_fft<N, E, false, true, RAD>(v, j, a.tw2, sm);
+    const float *Kr = krow(a, kx, row);
+    float2 u[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int k = j + r * T;
+        const int kf = k <= n2 ? k : N - k;
+        const float kv = act ? __ldg(Kr + kf) : 0.f;
+        v[r] = kv * v[r];
+        const float kk = wave(k, n2, a.k2s);
+        u[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
+    }
+    line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+    }
+    if (withE) {
+        line_fft<N, E, true, false, RAD>(u, j, a.tw2, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
+        }
+    }
+}
+
+// Adjoint: buf0 line V (and buf1 line Z when hasE) -> K (F2 V + i k2 F2 Z) -> inverse -> buf0.
+template <int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj(PassArgs a, int hasE)
+{
+    using C = RowCfg<N>;
+    constexpr int E = C::E, T = C::T, LPC = C::LPC;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const int lines = (a.n0 + 1) * a.rows1;
+    const int line = blockIdx.x * LPC + li;
+    const bool act = line < lines;
+    const int lc = act ? line : 0;
+    const int kx = lc / a.rows1, row = lc % a.rows1;
+    const int n2 = a.n2;
+    float2 *L0 = a.buf0 + (size_t)lc * n2;
+    float2 *L1 = a.buf1 + (size_t)lc * n2;
+    RowView<C::PAD> sm{smem + li * C::SPAN};
+    float2 v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        v[r] = make_float2(0.f, 0.f);
+        if (r < E / 2 && act) v[r] = L0[j + r * T];
+    }
+    line_fft<N, E, false, true, RAD>(v, j, a.tw2, sm);
+    if (hasE) {
+        float2 w[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            w[r] = make_float2(0.f, 0.f);
+            if (r < E / 2 && act) w[r] = L1[j + r * T];
+        }
+        line_fft<N, E, false, true, RAD>(w, j, a.tw2, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float kk = wave(j + r * T, n2, a.k2s);
+            v[r] = make_float2(v[r].x - kk * w[r].y, v[r].y + kk * w[r].x);
+        }
+    }
+    const float *Kr = krow(a, kx, row);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int k = j + r * T;
+        const int kf = k <= n2 ? k : N - k;
+        v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+    }
+    line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+    }
+}
+
+// ----------------------------------------------------------------- P4 (axis 1)
+
+// Forward: buf0 (phi stream, all rows) -> inverse -> rows [0,n1); with E also
+// -i k1 phi -> rows [n1,2n1) of buf0 and buf1 (E2 stream) -> rows [0,n1) of buf1.
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd(PassArgs a, int withE)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int kx = blockIdx.y;
+    const int z = blockIdx.x * BZ + col;
+    const bool act = z < a.n2;
+    const int zc = act ? z : 0;
+    const int n1 = a.n1;
+    ColView sm{smem + col, BZ};
+    float2 v[E], u[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        v[r] = a.buf0[iidx(a, kx, j + r * T, zc)];
+        const float kk = wave(j + r * T, n1, a.k1s);
+        u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+    }
+    line_fft<N, E, true, false, RAD>(v, j, a.tw1, sm);
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
+    }
+    if (withE) {
+        line_fft<N, E, true, false, RAD>(u, j, a.tw1, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = u[r];
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = a.buf1[iidx(a, kx, j + r * T, zc)];
+        line_fft<N, E, true, false, RAD>(v, j, a.tw1, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = v[r];
+        }
+    }
+}
+
+// ----------------------------------------------------------------- P5 (axis 0)
+
+// Forward: phi stream (buf0 rows [0,n1)) -> (phi, E0) via W = (1 + k0) P; E1/E2
+// streams -> (E1, E2) via W = Y + i Z (3D: Y = buf0 rows n1 + y, Z = buf1 rows
+// y; 2D: Y = buf1 row 0, Z absent).  Adjoint uses mode phi-only.
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd(PassArgs a)
+{
+    using C = ColCfg<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int y = blockIdx.y;
+    const int z = blockIdx.x * BZ + col;
+    const bool act = z < a.n2;
+    const int zc = act ? z : 0;
+    constexpr int NH = N / 2;
+    float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
+    ColView sm{smem + col, BZ};
+    if (phi || e0) {
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int src = k <= NH ? k : N - k;
+            float2 p = a.buf0[iidx(a, src, y, zc)];
+            if (k > NH) p.y = -p.y;
+            if (e0) {
+                const float kk = wave(k, NH, a.k0s);
+                p = (1.f + kk) * p;   // W = P + i (-i k0 P): Re -> phi, Im -> E0
+            }
+            v[r] = p;
+        }
+        line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const size_t g = gidx(a, j + r * T, y, z);
+                if (phi) phi[g] = v[r].x;
+                if (e0) e0[g] = v[r].y;
+            }
+        }
+    }
+    if (e1) {
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int src = k <= NH ? k : N - k;
+            float2 Y, Z = make_float2(0.f, 0.f);
+            if (a.three_d) {
+                Y = a.buf0[iidx(a, src, a.n1 + y, zc)];
+                Z = a.buf1[iidx(a, src, y, zc)];
+            } else {
+                Y = a.buf1[iidx(a, src, y, zc)];
+            }
+            if (k > NH) {
+                Y.y = -Y.y;
+                Z.y = -Z.y;
+            }
+            v[r] = make_float2(Y.x - Z.y, Y.y + Z.x);   // Y + i Z
+        }
+        line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const size_t g = gidx(a, j + r * T, y, z);
+                e1[g] = v[r].x;
+                if (a.three_d) e2[g] = v[r].y;
+            }
+        }
+    }
+}
+
+} // namespace fsp

@@ -1,0 +1,219 @@
+"""Python face of the solver: plans, solves, adjoints, batches, autograd.
+
+Argument marshalling only: every step of a solve runs in libfsp.so's CUDA
+kernels on the caller's current torch stream.  PyTorch provides device memory
+(outputs and the plan workspace) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+METHODS = {"he": _lib.FSP_HE, "vgf": _lib.FSP_VGF, "he_nearby": _lib.FSP_HE_NEARBY,
+           "he_cellavg": _lib.FSP_HE_CELLAVG}
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """One grid geometry: shape (nx, ny[, nz]) cells of spacing h, method 'vgf' or 'he'.
+
+    Creating it runs the FP64 kernel precomputation on the current CUDA device
+    and allocates the plan's workspace with torch.
+    """
+
+    def __init__(self, shape, h, method: str = "vgf", lam: float = 1.0, g0: float | None = None,
+                 device=None):
+        self.lib = _lib.load()
+        shape = tuple(int(s) for s in shape)
+        h = tuple(float(x) for x in (h if np.ndim(h) else [h] * len(shape)))
+        if len(shape) not in (2, 3) or len(h) != len(shape):
+            raise ValueError("shape/h must have 2 or 3 entries")
+        self.shape, self.h, self.method, self.dim = shape, h, method, len(shape)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        nz = shape[2] if self.dim == 3 else 0
+        hz = h[2] if self.dim == 3 else 0.0
+        with torch.cuda.device(self.device):
+            handle = self.lib.fsp_plan_create_ex(shape[0], shape[1], nz, h[0], h[1], hz, METHODS[method],
+                                                 _lib.FSP_F32, float(lam), float("nan") if g0 is None else g0)
+            if not handle:
+                raise _lib.FspError(self.lib.fsp_last_error(), f"fsp_plan_create{shape}")
+            self.handle = ctypes.c_void_p(handle)
+            nbytes = self.lib.fsp_plan_workspace_bytes(self.handle, 1, 1)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            _lib.check(self.lib.fsp_plan_set_workspace(self.handle, _ptr(self.workspace), nbytes),
+                       "fsp_plan_set_workspace")
+
+    # ----------------------------------------------------------------- info
+    def geometry(self) -> dict:
+        dim = ctypes.c_int()
+        n = (ctypes.c_int * 3)()
+        h = (ctypes.c_double * 3)()
+        L = ctypes.c_double()
+        M = (ctypes.c_int * 3)()
+        _lib.check(self.lib.fsp_plan_geometry(self.handle, ctypes.byref(dim), n, h, ctypes.byref(L), M),
+                   "fsp_plan_geometry")
+        d = dim.value
+        return {"dim": d, "n": list(n)[:d], "h": list(h)[:d], "L": L.value, "M": list(M)[:d]}
+
+    def kernel_spectrum(self) -> np.ndarray:
+        """FP32 kernel octant [nx+1][ny+1][(nz+1)] with prod(h)/prod(2n) folded in."""
+        shp = tuple(s + 1 for s in self.shape)
+        out = np.empty(shp, dtype=np.float32)
+        _lib.check(self.lib.fsp_plan_kernel_spectrum(self.handle, out.ctypes.data_as(ctypes.c_void_p), out.nbytes),
+                   "fsp_plan_kernel_spectrum")
+        return out
+
+    def set_pass_events(self, events):
+        """Record the given torch.cuda.Event objects at the pass boundaries of later solves (None: off)."""
+        if not events:
+            _lib.check(self.lib.fsp_plan_set_pass_events(self.handle, None, 0), "fsp_plan_set_pass_events")
+            return
+        handles = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+        _lib.check(self.lib.fsp_plan_set_pass_events(self.handle, handles, len(events)), "fsp_plan_set_pass_events")
+
+    @property
+    def passes(self) -> int:
+        return 5 if self.dim == 3 else 3
+
+    @property
+    def points(self) -> int:
+        return int(np.prod(self.shape))
+
+    # ---------------------------------------------------------------- solve
+    def _check_grid(self, t, name, lead=()):
+        want = tuple(lead) + self.shape
+        if t.dtype != torch.float32 or not t.is_cuda or tuple(t.shape) != want or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {want}")
+
+    def solve(self, rho, with_phi: bool = True, with_E: bool = True, phi=None, E=None, stream=None):
+        """phi, E for density rho (float32 CUDA tensor of the plan's shape)."""
+        self._check_grid(rho, "rho")
+        if with_phi and phi is None:
+            phi = torch.empty_like(rho)
+        if with_E and E is None:
+            E = torch.empty((self.dim,) + self.shape, dtype=torch.float32, device=rho.device)
+        _lib.check(self.lib.fsp_solve(self.handle, _ptr(rho), _ptr(phi if with_phi else None),
+                                      _ptr(E if with_E else None), _stream(stream)), "fsp_solve")
+        return (phi if with_phi else None), (E if with_E else None)
+
+    __call__ = solve
+
+    def adjoint(self, g_phi=None, g_E=None, g_rho=None, stream=None):
+        """g_rho = A^T g_phi + sum_a B_a^T g_E[a] (either input may be None)."""
+        if g_phi is None and g_E is None:
+            raise ValueError("need g_phi or g_E")
+        if g_phi is not None:
+            self._check_grid(g_phi, "g_phi")
+        if g_E is not None:
+            self._check_grid(g_E, "g_E", (self.dim,))
+        ref = g_phi if g_phi is not None else g_E
+        if g_rho is None:
+            g_rho = torch.empty(self.shape, dtype=torch.float32, device=ref.device)
+        _lib.check(self.lib.fsp_solve_adjoint(self.handle, _ptr(g_phi), _ptr(g_E), _ptr(g_rho), _stream(stream)),
+                   "fsp_solve_adjoint")
+        return g_rho
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fsp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _arr(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[p.value if p is not None else None for p in ptrs])
+
+
+def solve_batched(plans, rhos, with_phi: bool = True, with_E: bool = True, stream=None):
+    """Independent solves over several plans (distinct plans, one workspace each)."""
+    lib = _lib.load()
+    phis = [torch.empty_like(r) if with_phi else None for r in rhos]
+    Es = [torch.empty((p.dim,) + p.shape, dtype=torch.float32, device=r.device) if with_E else None
+          for p, r in zip(plans, rhos)]
+    for p, r in zip(plans, rhos):
+        p._check_grid(r, "rho")
+    hp = _arr([p.handle for p in plans])
+    _lib.check(lib.fsp_solve_batched(hp, len(plans), _arr([_ptr(r) for r in rhos]),
+                                     _arr([_ptr(x) for x in phis]) if with_phi else None,
+                                     _arr([_ptr(x) for x in Es]) if with_E else None, _stream(stream)),
+               "fsp_solve_batched")
+    return phis, Es
+
+
+class Batch:
+    """Prebuilt batch of independent solves with fixed input/output tensors (graph friendly)."""
+
+    def __init__(self, plans, rhos, with_phi: bool = True, with_E: bool = True):
+        self.lib = _lib.load()
+        self.plans, self.rhos = list(plans), list(rhos)
+        self.phis = [torch.empty_like(r) if with_phi else None for r in self.rhos]
+        self.Es = [torch.empty((p.dim,) + p.shape, dtype=torch.float32, device=r.device) if with_E else None
+                   for p, r in zip(self.plans, self.rhos)]
+        h = self.lib.fsp_batch_create(_arr([p.handle for p in self.plans]), len(self.plans),
+                                      _arr([_ptr(r) for r in self.rhos]),
+                                      _arr([_ptr(x) for x in self.phis]) if with_phi else None,
+                                      _arr([_ptr(x) for x in self.Es]) if with_E else None)
+        if not h:
+            raise _lib.FspError(self.lib.fsp_last_error(), "fsp_batch_create")
+        self.handle = ctypes.c_void_p(h)
+
+    def run(self, stream=None):
+        _lib.check(self.lib.fsp_batch_solve(self.handle, _stream(stream)), "fsp_batch_solve")
+        return self.phis, self.Es
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fsp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FspSolve(torch.autograd.Function):
+    """rho -> (phi, E) with the hand-written adjoint as backward.
+
+    The map is linear; its transpose is g_rho = A g_phi - sum_a B_a g_E[a]
+    (A symmetric, B_a antisymmetric), computed by fsp_solve_adjoint.
+    """
+
+    @staticmethod
+    def forward(ctx, rho, plan):
+        ctx.plan = plan
+        phi, E = plan.solve(rho.contiguous())
+        return phi, E
+
+    @staticmethod
+    def backward(ctx, g_phi, g_E):
+        plan = ctx.plan
+        if g_phi is None and g_E is None:
+            return None, None
+        g = plan.adjoint(None if g_phi is None else g_phi.contiguous(), None if g_E is None else g_E.contiguous())
+        return g, None
+
+
+def solve(rho, h, method: str = "vgf", with_E: bool = True):
+    """One-shot convenience: build a plan for rho's shape and solve."""
+    plan = Plan(tuple(rho.shape), h, method)
+    return plan.solve(rho, with_E=with_E)

@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every comparison runs both sides on the same seeded FP32 inputs (the oracle
+reads them as FP64).  Tolerance: relative L-inf <= 1e-5 for phi and for E
+(max |x - x_ref| / max |x_ref|), the accuracy the FP32 pipeline is built to.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import analytic as A
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fsp():
+    from paper_2103_08531_gb300 import build
+    build.build()
+    import paper_2103_08531_gb300 as pkg
+    pkg.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return pkg
+
+
+def rel(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(x - ref)) / np.max(np.abs(ref)))
+
+
+def gpu_solve(fsp, prob, method, with_E=True, **kw):
+    rho32 = prob.rho(np.float32)
+    plan = fsp.Plan(prob.shape, prob.h, method, **kw)
+    phi, E = plan.solve(torch.from_numpy(rho32).cuda(), with_E=with_E)
+    torch.cuda.synchronize()
+    return plan, rho32, phi.cpu().numpy(), (E.cpu().numpy() if E is not None else None)
+
+
+SMALL = [
+    ("cube32", (32, 32, 32), (2 / 32,) * 3),
+    ("aniso", (32, 64, 96), (0.03, 0.02, 0.011)),
+    ("flat", (64, 32, 32), (0.01, 0.03, 0.02)),
+    ("2d", (64, 128), (0.02, 0.011)),
+    ("2d_sq", (256, 256), (1 / 128, 1 / 128)),
+]
+
+
+def _mixture(shape, h, seed, count=3):
+    rng = np.random.default_rng(seed)
+    side = [n * hh for n, hh in zip(shape, h)]
+    gs = []
+    for _ in range(count):
+        c = np.array([rng.uniform(-0.25, 0.25) * s for s in side])
+        sig = np.array([rng.uniform(0.06, 0.12) * s for s in side])
+        gs.append((c, sig, rng.uniform(-1, 1)))
+    return W.Problem("mix", shape, h, gs)
+
+
+# ---------------------------------------------------------------- geometry
+
+@pytest.mark.parametrize("name,shape,h", SMALL + [("beam", (64, 64, 256), (0.005, 0.02, 0.03))])
+def test_geometry_rules_match_oracle(fsp, oracle_mod, name, shape, h):
+    plan = fsp.Plan(shape, h, "vgf")
+    g = plan.geometry()
+    L = oracle_mod.truncation_radius(shape, h)
+    assert g["n"] == list(shape)
+    assert abs(g["L"] - L) <= 1e-12 * L
+    assert g["M"] == oracle_mod.oversampled_size(shape, h, L)
+
+
+# ---------------------------------------------------------- kernel spectrum
+
+@pytest.mark.parametrize("method", ["he", "vgf", "he_nearby", "he_cellavg"])
+@pytest.mark.parametrize("name,shape,h", SMALL)
+def test_kernel_spectrum_parity(fsp, oracle_mod, method, name, shape, h):
+    """FP64 device precompute, rounded to FP32, vs the oracle's DFT of its kernel."""
+    plan = fsp.Plan(shape, h, method)
+    K = plan.kernel_spectrum().astype(np.float64)
+    if method == "vgf":
+        g = oracle_mod.kernel_vgf(list(shape), h)
+    else:
+        g = oracle_mod.kernel_he(list(shape), h, g0=oracle_mod.he_g0_variant(len(shape), h, method))
+    ref = oracle_mod.scaled_spectrum_octant(g, h)
+    assert K.shape == ref.shape
+    err = np.abs(K - ref)
+    assert np.all(err <= 2 ** -23 * np.abs(ref) + 1e-12 * np.max(np.abs(ref)))
+
+
+# --------------------------------------------------------------- solves
+
+@pytest.mark.parametrize("method", ["vgf", "he"])
+@pytest.mark.parametrize("name,shape,h", SMALL)
+def test_solve_parity(fsp, oracle_mod, method, name, shape, h):
+    prob = _mixture(shape, h, seed=hash(name) % 1000)
+    plan, rho32, phi, E = gpu_solve(fsp, prob, method)
+    g = oracle_mod.kernel(method, list(shape), h)
+    p_ref, E_ref = oracle_mod.solve_with_kernel(g, rho32.astype(np.float64), h)
+    assert rel(phi, p_ref) <= TOL
+    assert rel(E, E_ref) <= TOL
+    for a in range(len(shape)):
+        assert rel(E[a], E_ref[a]) <= 4 * TOL
+
+
+@pytest.mark.parametrize("name,shape,h", SMALL[:2] + SMALL[3:4])
+def test_phi_only_and_E_only(fsp, name, shape, h):
+    prob = _mixture(shape, h, seed=5)
+    rho = torch.from_numpy(prob.rho(np.float32)).cuda()
+    plan = fsp.Plan(shape, h, "vgf")
+    phi, E = plan.solve(rho)
+    phi1, none = plan.solve(rho, with_E=False)
+    none2, E1 = plan.solve(rho, with_phi=False)
+    assert none is None and none2 is None
+    assert rel(phi1.cpu(), phi.cpu()) <= 1e-6
+    assert rel(E1.cpu(), E.cpu()) <= 1e-6
+
+
+def test_c1_closed_form(fsp):
+    """32^3 unit Gaussian (sigma 0.15) on [-1,1]^3: the GPU VGF solve sits on the erf potential."""
+    prob = W.unit_gaussian_3d(32, 0.15, 2.0)
+    _, _, phi, E = gpu_solve(fsp, prob, "vgf")
+    pex, Eex = A.mixture_field(W.grid_points(prob.shape, prob.h), prob.gaussians, 3)
+    assert rel(phi, pex) < 3e-6 and rel(E, Eex) < 3e-6
+    _, _, phi_he, _ = gpu_solve(fsp, prob, "he")
+    assert rel(phi_he, pex) > 1e-3
+
+
+def test_2d_closed_form(fsp):
+    prob = W.unit_gaussian_2d(128, 0.05, 1.0)
+    _, _, phi, E = gpu_solve(fsp, prob, "vgf")
+    pex, Eex = A.mixture_field(W.grid_points(prob.shape, prob.h), prob.gaussians, 2)
+    assert rel(phi, pex) < 3e-6 and rel(E, Eex) < 3e-6
+
+
+# --------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("method", ["vgf", "he"])
+@pytest.mark.parametrize("name,shape,h", [SMALL[1], SMALL[3]])
+def test_adjoint_parity(fsp, oracle_mod, method, name, shape, h):
+    rng = np.random.default_rng(21)
+    d = len(shape)
+    gp = rng.standard_normal(shape).astype(np.float32)
+    gE = rng.standard_normal((d,) + shape).astype(np.float32)
+    plan = fsp.Plan(shape, h, method)
+    g = oracle_mod.kernel(method, list(shape), h)
+    got = plan.adjoint(torch.from_numpy(gp).cuda(), torch.from_numpy(gE).cuda()).cpu().numpy()
+    ref = oracle_mod.adjoint_with_kernel(g, gp.astype(np.float64), gE.astype(np.float64), h)
+    assert rel(got, ref) <= TOL
+    got_e = plan.adjoint(None, torch.from_numpy(gE).cuda()).cpu().numpy()
+    ref_e = oracle_mod.adjoint_with_kernel(g, None, gE.astype(np.float64), h)
+    assert rel(got_e, ref_e) <= TOL
+    got_p = plan.adjoint(torch.from_numpy(gp).cuda(), None).cpu().numpy()
+    ref_p = oracle_mod.adjoint_with_kernel(g, gp.astype(np.float64), None, h)
+    assert rel(got_p, ref_p) <= TOL
+
+
+@pytest.mark.parametrize("name,shape,h", [SMALL[0], SMALL[4]])
+def test_adjoint_dot_product(fsp, name, shape, h):
+    """<(phi, E)(rho), (psi, chi)> == <rho, adjoint(psi, chi)> with the GPU on both sides."""
+    rng = np.random.default_rng(22)
+    d = len(shape)
+    rho = torch.from_numpy(rng.standard_normal(shape).astype(np.float32)).cuda()
+    psi = torch.from_numpy(rng.standard_normal(shape).astype(np.float32)).cuda()
+    chi = torch.from_numpy(rng.standard_normal((d,) + shape).astype(np.float32)).cuda()
+    plan = fsp.Plan(shape, h, "vgf")
+    phi, E = plan.solve(rho)
+    g = plan.adjoint(psi, chi)
+    lhs = (phi.double() * psi.double()).sum() + (E.double() * chi.double()).sum()
+    rhs = (rho.double() * g.double()).sum()
+    scale = (phi.double().abs() * psi.double().abs()).sum() + (E.double().abs() * chi.double().abs()).sum()
+    assert abs(float(lhs - rhs)) <= 1e-6 * float(scale)
+
+
+def test_autograd_matches_fd_and_oracle_gradient(fsp, oracle_mod):
+    """loss = sum (phi - phi_t)^2 + 0.1 sum |E|^2: FspSolve backward vs FP64 central differences."""
+    n, B = 32, 2
+    probs, target = W.training_batch(n, B, seeds=range(10, 10 + B))
+    h = probs[0].h
+    plan = fsp.Plan((n, n, n), h, "vgf")
+    tgt = torch.from_numpy(target).cuda()
+    g2n = oracle_mod.kernel_vgf([n, n, n], h)
+    rng = np.random.default_rng(5)
+    for prob in probs:
+        rho32 = prob.rho(np.float32)
+        rho = torch.from_numpy(rho32).cuda().requires_grad_(True)
+        phi, E = fsp.FspSolve.apply(rho, plan)
+        loss = ((phi - tgt) ** 2).sum() + 0.1 * (E ** 2).sum()
+        loss.backward()
+        grad = rho.grad.cpu().numpy().astype(np.float64)
+
+        r64 = rho32.astype(np.float64)
+        t64 = target.astype(np.float64)
+
+        def L(r):
+            p, e = oracle_mod.solve_with_kernel(g2n, r, h)
+            return np.sum((p - t64) ** 2) + 0.1 * np.sum(e ** 2)
+
+        p0, e0 = oracle_mod.solve_with_kernel(g2n, r64, h)
+        ref = oracle_mod.adjoint_with_kernel(g2n, 2 * (p0 - t64), 0.2 * e0, h)
+        assert rel(grad, ref) <= 2 * TOL
+        eps = 1e-2 * np.max(np.abs(r64))
+        for idx in map(tuple, rng.integers(0, n, size=(32, 3))):
+            rp, rm = r64.copy(), r64.copy()
+            rp[idx] += eps
+            rm[idx] -= eps
+            fd = (L(rp) - L(rm)) / (2 * eps)
+            assert abs(grad[idx] - fd) <= 2 * TOL * np.max(np.abs(ref))
+
+
+# --------------------------------------------------------------- batches
+
+def test_batched_equals_single(fsp):
+    shapes = [((32, 32, 32), (0.02, 0.03, 0.025)), ((64, 32, 32), (0.01, 0.02, 0.03)),
+              ((32, 64, 96), (0.03, 0.01, 0.02)), ((32, 32, 128), (0.02, 0.02, 0.005))]
+    plans, rhos = [], []
+    for i, (s, h) in enumerate(shapes):
+        plans.append(fsp.Plan(s, h, "vgf"))
+        rhos.append(torch.from_numpy(_mixture(s, h, 40 + i).rho(np.float32)).cuda())
+    phis, Es = fsp.solve_batched(plans, rhos)
+    batch = fsp.Batch(plans, rhos)
+    bphis, bEs = batch.run()
+    for p, r, ph, E, bph, bE in zip(plans, rhos, phis, Es, bphis, bEs):
+        ph1, E1 = p.solve(r)
+        assert torch.equal(ph, ph1) and torch.equal(E, E1)
+        assert torch.equal(bph, ph1) and torch.equal(bE, E1)
+
+
+# ------------------------------------------------------------ full sizes
+
+def test_full_size_256_vgf_against_oracle(fsp, oracle_mod):
+    """The 256^3 FP32 mixture (8 anisotropic Gaussians, seed 1) against the FP64 oracle, every cell."""
+    prob = W.mixture_3d(256, 8, 1)
+    plan, rho32, phi, E = gpu_solve(fsp, prob, "vgf")
+    g = oracle_mod.kernel_vgf(list(prob.shape), prob.h)
+    K = plan.kernel_spectrum().astype(np.float64)
+    ref_K = oracle_mod.scaled_spectrum_octant(g, prob.h)
+    assert np.all(np.abs(K - ref_K) <= 2 ** -23 * np.abs(ref_K) + 1e-12 * np.max(np.abs(ref_K)))
+    p_ref, E_ref = oracle_mod.solve_with_kernel(g, rho32.astype(np.float64), prob.h)
+    assert rel(phi, p_ref) <= TOL
+    assert rel(E, E_ref) <= TOL
+
+
+def test_full_size_256_he_sampled(fsp, oracle_mod):
+    """HE at 256^3: phi at 48 sampled cells against the brute-force sum."""
+    prob = W.mixture_3d(256, 8, 1)
+    _, rho32, phi, _ = gpu_solve(fsp, prob, "he", with_E=False)
+    g = oracle_mod.kernel_he(list(prob.shape), prob.h)
+    pts = np.random.default_rng(7).integers(0, phi.size, size=48)
+    ref = oracle_mod.direct_phi_at(g, rho32.astype(np.float64), prob.h, pts)
+    assert np.max(np.abs(phi.ravel()[pts] - ref)) <= TOL * np.max(np.abs(phi))
+
+
+def test_full_size_2d_closed_form(fsp):
+    """4096^2 mixture of 16 isotropic Gaussians: VGF vs the E1 closed form at every cell."""
+    prob = W.mixture_2d(4096, 16, 2)
+    _, _, phi, E = gpu_solve(fsp, prob, "vgf")
+    pts = W.grid_points(prob.shape, prob.h)
+    sl = (slice(None, None, 7), slice(None, None, 5))
+    pex, Eex = A.mixture_field(pts[sl], prob.gaussians, 2)
+    assert rel(phi[sl], pex) < 2e-5
+    assert rel(E[(slice(None),) + sl], Eex) < 2e-5
+
+
+def test_full_size_linearity_and_translation(fsp):
+    """Properties at 256^3 that hold at any size: linearity, whole-cell translation."""
+    prob = W.mixture_3d(256, 8, 1)
+    plan = fsp.Plan(prob.shape, prob.h, "vgf")
+    rho = torch.from_numpy(prob.rho(np.float32)).cuda()
+    phi, E = plan.solve(rho)
+    phi2, E2 = plan.solve(2.0 * rho)
+    assert rel((phi2 / 2).cpu(), phi.cpu()) <= 1e-6
+    comp = torch.zeros_like(rho)
+    comp[40:120, 60:140, 30:110] = rho[40:120, 60:140, 30:110]
+    pa, Ea = plan.solve(comp)
+    pb, Eb = plan.solve(torch.roll(comp, shifts=(17, -9, 23), dims=(0, 1, 2)))
+    assert rel(pb[17:, :-9, 23:].cpu(), pa[:-17, 9:, :-23].cpu()) <= 2e-6
+    assert rel(Eb[:, 17:, :-9, 23:].cpu(), Ea[:, :-17, 9:, :-23].cpu()) <= 2e-6

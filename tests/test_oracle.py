@@ -351,3 +351,24 @@ def test_golden_c1_samples(oracle_mod):
     cf = np.array(gold["closed_form"]["phi"])
     assert np.max(np.abs(np.array(gold["vgf"]["phi"]) - cf)) < 1e-7 * np.max(np.abs(cf))
     assert np.max(np.abs(np.array(gold["he"]["phi"]) - cf)) > 1e-4 * np.max(np.abs(cf))
+
+
+def test_direct_sum_at_points_matches_full_direct_sum(oracle_mod):
+    shape, h = (6, 7, 8), (0.1, 0.2, 0.15)
+    rho = np.random.default_rng(13).standard_normal(shape)
+    g = oracle_mod.kernel_vgf(list(shape), h)
+    full = oracle_mod.direct_phi(g, rho, h)
+    pts = np.array([0, 5, 17, 100, 335])
+    assert np.max(np.abs(oracle_mod.direct_phi_at(g, rho, h, pts) - full.ravel()[pts])) < 1e-13 * np.max(np.abs(full))
+
+
+def test_he_cell_average_constants(oracle_mod):
+    """Cell-average G(0): unit cube int 1/|x| = 2.380077..., unit square int ln|x| = -1.061175..."""
+    g3 = oracle_mod.he_g0_variant(3, (1.0, 1.0, 1.0), "he_cellavg")
+    assert abs(g3 * 4 * math.pi - 2.3800772) < 1e-6
+    g2 = oracle_mod.he_g0_variant(2, (1.0, 1.0), "he_cellavg")
+    assert abs(-g2 * 2 * math.pi - (-1.0611759)) < 1e-6
+    # nearby value is G at the smallest spacing
+    assert oracle_mod.he_g0_variant(3, (0.1, 0.2, 0.3), "he_nearby") == pytest.approx(1 / (4 * math.pi * 0.1))
+    # cell average scales like 1/h in 3D
+    assert oracle_mod.he_g0_variant(3, (0.5, 0.5, 0.5), "he_cellavg") == pytest.approx(2 * g3, rel=1e-9)
