@@ -192,7 +192,14 @@ def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return 0
-    n = 128
+    # size each step's sample so the whole run stays within about two minutes
+    t64, _, _ = oracle_sample(64)
+    budget = 120.0 / (args.steps + args.warmup)
+    n = 32
+    for cand in (128, 64):
+        if t64[0] * (cand / 64) ** 3 * 1.2 <= budget:
+            n = cand
+            break
     for _ in range(args.warmup):
         oracle_sample(n)
     times, scale, cores = [], None, None
@@ -205,7 +212,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "3D VGF 256^3 on [-1,1]^3, 8 anisotropic Gaussians (seed 1), "
-                                                        "phi+E; CPU sample at 128^3 scaled by N^3 log N"},
+                                                        f"phi+E; CPU sample at {n}^3 scaled by N^3 log N"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} FP64 oracle phi+E solves at {n}^3, each scaled to 256^3 "
                                        f"by the work ratio {scale:.2f}"},
