@@ -232,24 +232,75 @@ struct RowSpan {
     static constexpr int value = N + (N >> PAD) + 1;
 };
 
+// ------------------------------------------------------------------ cp.async
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------- passes
+
+enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
+// Twiddle sources: TW_TABLE loads each W^(r m) from the table (cheap when the
+// lanes of a warp share m, as in column tiles); TW_POW loads W^m, W^2m, W^4m,
+// W^8m and forms the other powers by products (lanes with distinct m).
+enum { TW_TABLE = 0, TW_POW = 1 };
+
+template <int SYNC>
+__device__ __forceinline__ void lsync()
+{
+    if constexpr (SYNC == SYNC_WARP) __syncwarp();
+    else __syncthreads();
+}
+
+// u[r] *= W^(r m) (conjugated for the inverse), r = 1 .. R-1.
+template <int R, bool INV, int TW>
+__device__ __forceinline__ void twiddle(float2 *u, const float2 *__restrict__ tw, int m)
+{
+    if constexpr (TW == TW_TABLE || R <= 3) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + r * m));
+    } else {
+        float2 w[R];
+        w[1] = __ldg(tw + m);
+        w[2] = __ldg(tw + 2 * m);
+        w[3] = cmul(w[1], w[2]);
+        if constexpr (R >= 8) {
+            w[4] = __ldg(tw + 4 * m);
+            w[5] = cmul(w[1], w[4]);
+            w[6] = cmul(w[2], w[4]);
+            w[7] = cmul(w[3], w[4]);
+        }
+        if constexpr (R >= 16) {
+            w[8] = __ldg(tw + 8 * m);
+#pragma unroll
+            for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+        }
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], w[r]);
+    }
+}
 
 template <int... RS>
 struct Radices {};
 
-template <int N, int E, bool INV, int NS, class RAD>
+template <int N, int E, bool INV, int NS, class RAD, int SYNC, int TW>
 struct Passes;
 
-template <int N, int E, bool INV, int NS>
-struct Passes<N, E, INV, NS, Radices<>> {
+template <int N, int E, bool INV, int NS, int SYNC, int TW>
+struct Passes<N, E, INV, NS, Radices<>, SYNC, TW> {
     template <bool PRUNE, class View>
     static __device__ __forceinline__ void run(float2 (&)[E], int, const float2 *__restrict__, const View &)
     {
     }
 };
 
-template <int N, int E, bool INV, int NS, int R, int... RS>
-struct Passes<N, E, INV, NS, Radices<R, RS...>> {
+template <int N, int E, bool INV, int NS, int R, int... RS, int SYNC, int TW>
+struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW> {
     template <bool PRUNE, class View>
     static __device__ __forceinline__ void run(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
     {
@@ -264,11 +315,7 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>> {
             float2 u[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) u[r] = v[q + r * Q];
-            if constexpr (NS > 1) {
-                constexpr int STEP = N / (NS * R);
-#pragma unroll
-                for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + r * k * STEP));
-            }
+            if constexpr (NS > 1) twiddle<R, INV, TW>(u, tw, k * (N / (NS * R)));
             if constexpr (PRUNE && NS == 1) dft_half_in<R, INV>(u);
             else dft<R, INV>(u);
             if constexpr (LAST) {
@@ -281,25 +328,25 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>> {
             }
         }
         if constexpr (!LAST) {
-            __syncthreads();
+            lsync<SYNC>();
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = sm.at(j + r * T);
-            __syncthreads();
-            Passes<N, E, INV, NS * R, Radices<RS...>>::template run<false>(v, j, tw, sm);
+            lsync<SYNC>();
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW>::template run<false>(v, j, tw, sm);
         }
     }
 };
 
-// Whole-line transform.  Precondition: every thread of the block calls it (it
-// contains __syncthreads) and nobody still reads the shared buffer.  On return
-// the shared buffer is free again.
-template <int N, int E, bool INV, bool PRUNE_IN, class RAD, class View>
+// Whole-line transform.  Precondition: every thread of the sync group (block
+// or warp) calls it and nobody still reads the shared buffer.  On return the
+// shared buffer is free again.
+template <int N, int E, bool INV, bool PRUNE_IN, class RAD, class View, int SYNC = SYNC_BLOCK, int TW = TW_TABLE>
 __device__ __forceinline__ void line_fft(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
 {
-    Passes<N, E, INV, 1, RAD>::template run<PRUNE_IN>(v, j, tw, sm);
+    Passes<N, E, INV, 1, RAD, SYNC, TW>::template run<PRUNE_IN>(v, j, tw, sm);
 }
 
-// Radix plans per padded length (E values per thread).
+// Radix plans per padded length for block-synchronous tiles (E values per thread).
 template <int N>
 struct Plan1D;
 template <> struct Plan1D<64> { static constexpr int E = 8; using R = Radices<8, 8>; };
@@ -312,5 +359,14 @@ template <> struct Plan1D<1024> { static constexpr int E = 16; using R = Radices
 template <> struct Plan1D<2048> { static constexpr int E = 16; using R = Radices<16, 16, 8>; };
 template <> struct Plan1D<4096> { static constexpr int E = 16; using R = Radices<16, 16, 16>; };
 template <> struct Plan1D<8192> { static constexpr int E = 16; using R = Radices<16, 8, 8, 8>; };
+
+// Radix plans for 16-values-per-thread work (one warp or less per line).
+template <int N>
+struct Plan16;
+template <> struct Plan16<64> { static constexpr int E = 8; using R = Radices<8, 8>; };
+template <> struct Plan16<128> { static constexpr int E = 16; using R = Radices<16, 8>; };
+template <> struct Plan16<192> { static constexpr int E = 12; using R = Radices<4, 4, 4, 3>; };
+template <> struct Plan16<256> { static constexpr int E = 16; using R = Radices<16, 16>; };
+template <> struct Plan16<512> { static constexpr int E = 16; using R = Radices<16, 16, 2>; };
 
 } // namespace fsp

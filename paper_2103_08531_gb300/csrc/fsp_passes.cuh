@@ -80,7 +80,7 @@ struct RowCfg {
 
 // Forward: rho columns (z, z+1) packed as re/im; output rows 0..n1-1 of buf_out.
 template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd(PassArgs a, float2 *__restrict__ dst)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_blk(PassArgs a, float2 *__restrict__ dst)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_adj(PassArgs a)
 
 // Forward: src rows 0..n1-1 -> dst rows 0..2n1-1.
 template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd(PassArgs a, const float2 *__restrict__ src, float2 *__restrict__ dst)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd_blk(PassArgs a, const float2 *__restrict__ src, float2 *__restrict__ dst)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
@@ -272,7 +272,7 @@ __device__ __forceinline__ const float *krow(const PassArgs &a, int kx, int row)
 // Forward: line of buf0 -> F2 -> x K -> inverse -> buf0 (phi stream), and
 // -i k2 K -> inverse -> buf1 (E2 stream) when withE.
 template <int N>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd(PassArgs a, int withE)
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(PassArgs a, int withE)
 {
     using C = RowCfg<N>;
     constexpr int E = C::E, T = C::T, LPC = C::LPC;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd(PassArgs a, int wit
 
 // Adjoint: buf0 line V (and buf1 line Z when hasE) -> K (F2 V + i k2 F2 Z) -> inverse -> buf0.
 template <int N>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj(PassArgs a, int hasE)
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj_blk(PassArgs a, int hasE)
 {
     using C = RowCfg<N>;
     constexpr int E = C::E, T = C::T, LPC = C::LPC;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj(PassArgs a, int has
 // Forward: buf0 (phi stream, all rows) -> inverse -> rows [0,n1); with E also
 // -i k1 phi -> rows [n1,2n1) of buf0 and buf1 (E2 stream) -> rows [0,n1) of buf1.
 template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd(PassArgs a, int withE)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd_blk(PassArgs a, int withE)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd(PassArgs a, int wit
 // streams -> (E1, E2) via W = Y + i Z (3D: Y = buf0 rows n1 + y, Z = buf1 rows
 // y; 2D: Y = buf1 row 0, Z absent).  Adjoint uses mode phi-only.
 template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd(PassArgs a)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(PassArgs a)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
@@ -490,6 +490,398 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd(PassArgs a)
                 e1[g] = v[r].x;
                 if (a.three_d) e2[g] = v[r].y;
             }
+        }
+    }
+}
+
+
+
+// =====================================================================
+// Persistent, cp.async-staged column passes (2 n <= 512) and warp-per-line
+// middle pass.  A column tile is 16 consecutive axis-2 columns by the whole
+// line; T = N / E threads per column (E = 16 values per thread), lanes
+// across columns so every global row access is 128 B or wider.  The CTA
+// loops over tiles; the next tile is copied into shared memory with cp.async
+// while the current one is transformed, so loads overlap the arithmetic.
+// =====================================================================
+
+template <int N>
+struct TileCfg {
+    static constexpr int E = Plan16<N>::E;
+    static constexpr int T = N / E;
+    static constexpr int C = 16;
+    static constexpr int THREADS = T * C;
+    using RAD = typename Plan16<N>::R;
+    static constexpr int EX = N * C;   // exchange buffer, float2
+};
+
+// Rows [0, nrows) of 128 B each (16 complex or 32 real) into dst (row r at dst + 16 r).
+__device__ __forceinline__ void issue_rows(float2 *dst, const void *src, size_t row_bytes_stride, int nrows, int tid,
+                                           int nthr)
+{
+    const char *s = reinterpret_cast<const char *>(src);
+    for (int c = tid; c < nrows * 8; c += nthr) {
+        const int r = c >> 3, part = c & 7;
+        cp_async16(dst + r * 16 + part * 2, s + (size_t)r * row_bytes_stride + part * 16);
+    }
+}
+
+// P1: rho pairs (z, z+1) -> half spectrum in k0, output rows 0..n1-1 of dst.
+template <int N>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(PassArgs a, float2 *__restrict__ dst)
+{
+    using C = TileCfg<N>;
+    constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    float2 *stage = smem, *ex = smem + NH * 16;
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
+    const int zt = a.n2 / 32, ntiles = a.n1 * zt;
+    const size_t rstride = (size_t)a.n1 * a.n2 * sizeof(float);
+    auto issue = [&](int t) {
+        const int y = t / zt, z0 = (t % zt) * 32;
+        issue_rows(stage, a.in[0] + gidx(a, 0, y, z0), rstride, NH, tid, C::THREADS);
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) issue(t);
+    cp_async_commit();
+    ColView sm{ex + col, 16};
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int y = t / zt, z0 = (t % zt) * 32 + 2 * col;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * 16 + col] : make_float2(0.f, 0.f);
+        __syncthreads();
+        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        cp_async_commit();
+        line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r <= E / 2; ++r) {
+            const int k = j + r * T;
+            if (k <= NH) {
+                const float2 w = v[r];
+                const float2 m = sm.at(k == 0 ? 0 : N - k);
+                float4 o;
+                o.x = 0.5f * (w.x + m.x);
+                o.y = 0.5f * (w.y - m.y);
+                o.z = 0.5f * (w.y + m.y);
+                o.w = -0.5f * (w.x - m.x);
+                *reinterpret_cast<float4 *>(dst + iidx(a, k, y, z0)) = o;
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+// P2: buf_src rows 0..n1-1 -> forward axis 1 -> dst rows 0..2n1-1.
+template <int N>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(PassArgs a, const float2 *__restrict__ src,
+                                                              float2 *__restrict__ dst)
+{
+    using C = TileCfg<N>;
+    constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    float2 *stage = smem, *ex = smem + NH * 16;
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
+    const int zt = a.n2 / 16, ntiles = (a.n0 + 1) * zt;
+    const size_t rstride = (size_t)a.n2 * sizeof(float2);
+    auto issue = [&](int t) {
+        const int kx = t / zt, z0 = (t % zt) * 16;
+        issue_rows(stage, src + iidx(a, kx, 0, z0), rstride, NH, tid, C::THREADS);
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) issue(t);
+    cp_async_commit();
+    ColView sm{ex + col, 16};
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int kx = t / zt, z = (t % zt) * 16 + col;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * 16 + col] : make_float2(0.f, 0.f);
+        __syncthreads();
+        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        cp_async_commit();
+        line_fft<N, E, false, true, RAD>(v, j, a.tw1, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) dst[iidx(a, kx, j + r * T, z)] = v[r];
+    }
+    cp_async_wait_all();
+}
+
+// P4: buf0 (phi stream, 2 n1 rows) -> rows [0,n1) phi, rows [n1,2n1) -i k1 phi;
+// buf1 (E2 stream) -> rows [0,n1).
+template <int N>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(PassArgs a, int withE)
+{
+    using C = TileCfg<N>;
+    constexpr int E = C::E, T = C::T;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    float2 *st0 = smem, *st1 = smem + N * 16, *ex = smem + 2 * N * 16;
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
+    const int n1 = a.n1, zt = a.n2 / 16, ntiles = (a.n0 + 1) * zt;
+    const size_t rstride = (size_t)a.n2 * sizeof(float2);
+    auto issue = [&](int t) {
+        const int kx = t / zt, z0 = (t % zt) * 16;
+        issue_rows(st0, a.buf0 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
+        if (withE) issue_rows(st1, a.buf1 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) issue(t);
+    cp_async_commit();
+    ColView sm{ex + col, 16};
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int kx = t / zt, z = (t % zt) * 16 + col;
+        float2 v[E], w[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = st0[(j + r * T) * 16 + col];
+            w[r] = withE ? st1[(j + r * T) * 16 + col] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        cp_async_commit();
+        if (withE) {
+            line_fft<N, E, true, false, RAD>(w, j, a.tw1, sm);
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = w[r];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float kk = wave(j + r * T, n1, a.k1s);
+                w[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+            }
+            line_fft<N, E, true, false, RAD>(w, j, a.tw1, sm);
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = w[r];
+        }
+        line_fft<N, E, true, false, RAD>(v, j, a.tw1, sm);
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
+    }
+    cp_async_wait_all();
+}
+
+// P5: half spectra in k0 -> real outputs (see the header comment).
+template <int N>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
+{
+    using C = TileCfg<N>;
+    constexpr int E = C::E, T = C::T, NH = N / 2, ROWS = N / 2 + 1;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    float2 *sA = smem, *sB = smem + ROWS * 16, *sC = smem + 2 * ROWS * 16, *ex = smem + 3 * ROWS * 16;
+    float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
+    const bool first = phi || e0, second = e1 != nullptr;
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
+    const int zt = a.n2 / 16, ntiles = a.n1 * zt;
+    const size_t rstride = (size_t)a.rows1 * a.n2 * sizeof(float2);
+    auto issue = [&](int t) {
+        const int y = t / zt, z0 = (t % zt) * 16;
+        if (first) issue_rows(sA, a.buf0 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+        if (second) {
+            if (a.three_d) {
+                issue_rows(sB, a.buf0 + iidx(a, 0, a.n1 + y, z0), rstride, ROWS, tid, C::THREADS);
+                issue_rows(sC, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+            } else {
+                issue_rows(sB, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+            }
+        }
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) issue(t);
+    cp_async_commit();
+    ColView sm{ex + col, 16};
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int y = t / zt, z = (t % zt) * 16 + col;
+        float2 v[E], w[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int src = k <= NH ? k : N - k;
+            float2 p = make_float2(0.f, 0.f), Y = p, Z = p;
+            if (first) p = sA[src * 16 + col];
+            if (second) {
+                Y = sB[src * 16 + col];
+                if (a.three_d) Z = sC[src * 16 + col];
+            }
+            if (k > NH) {
+                p.y = -p.y;
+                Y.y = -Y.y;
+                Z.y = -Z.y;
+            }
+            if (e0) p = (1.f + wave(k, NH, a.k0s)) * p;   // W = P + i (-i k0 P)
+            v[r] = p;
+            w[r] = make_float2(Y.x - Z.y, Y.y + Z.x);        // Y + i Z
+        }
+        __syncthreads();
+        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        cp_async_commit();
+        if (first) {
+            line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const size_t g = gidx(a, j + r * T, y, z);
+                if (phi) phi[g] = v[r].x;
+                if (e0) e0[g] = v[r].y;
+            }
+        }
+        if (second) {
+            line_fft<N, E, true, false, RAD>(w, j, a.tw0, sm);
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const size_t g = gidx(a, j + r * T, y, z);
+                e1[g] = w[r].x;
+                if (a.three_d) e2[g] = w[r].y;
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+// ------------------------------------------------- warp-per-line middle pass
+
+template <int N>
+struct WarpCfg {
+    static constexpr int E = Plan16<N>::E;
+    static constexpr int T = N / E;
+    static constexpr int LPW = 32 / T;     // lines per warp
+    static constexpr int WARPS = 4;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int PAD = 4;
+    static constexpr int SPAN = RowSpan<N, PAD>::value;
+    using RAD = typename Plan16<N>::R;
+    static constexpr size_t SMEM = (size_t)SPAN * LPW * WARPS * sizeof(float2);
+};
+
+// Forward middle pass, one warp per line (or per 32/T lines), persistent over
+// lines with the next line's input prefetched into registers.
+template <int N>
+__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd(PassArgs a, int withE)
+{
+    using C = WarpCfg<N>;
+    constexpr int E = C::E, T = C::T, LPW = C::LPW;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int li = lane / T, j = lane % T;
+    const int n2 = a.n2;
+    const int lines = (a.n0 + 1) * a.rows1;
+    const int groups = (lines + LPW - 1) / LPW;
+    const int gstride = gridDim.x * C::WARPS;
+    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
+    int g = blockIdx.x * C::WARPS + warp;
+    float2 pv[E / 2];
+    {
+        const int line = g * LPW + li;
+        const bool act = g < groups && line < lines;
+        const float2 *L = a.buf0 + (size_t)(act ? line : 0) * n2;
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
+    }
+    for (; g < groups; g += gstride) {
+        const int line = g * LPW + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
+        {
+            const int ng = g + gstride;
+            const int nline = ng * LPW + li;
+            const bool nact = ng < groups && nline < lines;
+            const float2 *L = a.buf0 + (size_t)(nact ? nline : 0) * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r)
+                if (nact) pv[r] = L[j + r * T];
+        }
+        const int kx = lc / a.rows1, row = lc % a.rows1;
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        const float *Kr = krow(a, kx, row);
+        float2 u[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int kf = k <= n2 ? k : N - k;
+            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+            const float kk = wave(k, n2, a.k2s);
+            u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+        }
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        if (act) {
+            float2 *L0 = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+        }
+        if (withE) {
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(u, j, a.tw2, sm);
+            if (act) {
+                float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
+            }
+        }
+    }
+}
+
+// Adjoint middle pass, warp per line.
+template <int N>
+__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(PassArgs a, int hasE)
+{
+    using C = WarpCfg<N>;
+    constexpr int E = C::E, T = C::T, LPW = C::LPW;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int li = lane / T, j = lane % T;
+    const int n2 = a.n2;
+    const int lines = (a.n0 + 1) * a.rows1;
+    const int groups = (lines + LPW - 1) / LPW;
+    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
+    for (int g = blockIdx.x * C::WARPS + warp; g < groups; g += gridDim.x * C::WARPS) {
+        const int line = g * LPW + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
+        float2 *L0 = a.buf0 + (size_t)lc * n2;
+        float2 *L1 = a.buf1 + (size_t)lc * n2;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = (r < E / 2 && act) ? L0[j + r * T] : make_float2(0.f, 0.f);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        if (hasE) {
+            float2 w[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) w[r] = (r < E / 2 && act) ? L1[j + r * T] : make_float2(0.f, 0.f);
+            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(w, j, a.tw2, sm);
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float kk = wave(j + r * T, n2, a.k2s);
+                v[r] = make_float2(v[r].x - kk * w[r].y, v[r].y + kk * w[r].x);
+            }
+        }
+        const int kx = lc / a.rows1, row = lc % a.rows1;
+        const float *Kr = krow(a, kx, row);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int kf = k <= n2 ? k : N - k;
+            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+        }
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
         }
     }
 }
