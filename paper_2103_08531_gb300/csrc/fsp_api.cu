@@ -167,10 +167,10 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     }
     int rc = FSP_OK;
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
-    if (cudaMalloc(&p.tw0, sizeof(float2) * N0) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    if (cudaMalloc(&p.tw0, sizeof(float2) * (N0 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
     if (rc == FSP_OK) {
         if (dim == 3 && N1 != N0) {
-            if (cudaMalloc(&p.tw1, sizeof(float2) * N1) != cudaSuccess) rc = FSP_ERR_NOMEM;
+            if (cudaMalloc(&p.tw1, sizeof(float2) * (N1 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
         } else {
             p.tw1 = p.tw0;
         }
@@ -178,16 +178,19 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     if (rc == FSP_OK) {
         if (N2 == N0) p.tw2 = p.tw0;
         else if (dim == 3 && N2 == N1) p.tw2 = p.tw1;
-        else if (cudaMalloc(&p.tw2, sizeof(float2) * N2) != cudaSuccess) rc = FSP_ERR_NOMEM;
+        else if (cudaMalloc(&p.tw2, sizeof(float2) * (N2 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
     }
     p.K_count = (size_t)(p.n[0] + 1) * (p.n[1] + 1) * (dim == 3 ? (p.n[2] + 1) : 1);
     if (rc == FSP_OK && cudaMalloc(&p.K, sizeof(float) * p.K_count) != cudaSuccess) rc = FSP_ERR_NOMEM;
     cudaStream_t st = nullptr;
     if (rc == FSP_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = FSP_ERR_CUDA;
     if (rc == FSP_OK) {
-        if (make_twiddles(p.tw0, N0, st)) rc = FSP_ERR_CUDA;
-        if (rc == FSP_OK && p.tw1 != p.tw0 && make_twiddles(p.tw1, N1, st)) rc = FSP_ERR_CUDA;
-        if (rc == FSP_OK && p.tw2 != p.tw0 && p.tw2 != p.tw1 && make_twiddles(p.tw2, N2, st)) rc = FSP_ERR_CUDA;
+        if (make_twiddles(p.tw0, N0, st) || make_twiddles_aux(p.tw0, N0, st)) rc = FSP_ERR_CUDA;
+        if (rc == FSP_OK && p.tw1 != p.tw0 && (make_twiddles(p.tw1, N1, st) || make_twiddles_aux(p.tw1, N1, st)))
+            rc = FSP_ERR_CUDA;
+        if (rc == FSP_OK && p.tw2 != p.tw0 && p.tw2 != p.tw1 &&
+            (make_twiddles(p.tw2, N2, st) || make_twiddles_aux(p.tw2, N2, st)))
+            rc = FSP_ERR_CUDA;
     }
     if (rc == FSP_OK) rc = build_kernel_spectrum(&p, st);
     if (st) cudaStreamDestroy(st);

@@ -25,9 +25,9 @@ struct Occ0 {
 };
 
 template <int N>
-static constexpr size_t smem_p1() { return (size_t)(N / 2 * 16 + TileCfg<N>::EX) * sizeof(float2); }
+static constexpr size_t smem_p1() { return (size_t)(N / 2 * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 template <int N>
-static constexpr size_t smem_p5() { return (size_t)(3 * (N / 2 + 1) * 16 + TileCfg<N>::EX) * sizeof(float2); }
+static constexpr size_t smem_p5() { return (size_t)(3 * (N / 2 + 1) * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 
 template <int N>
 static int prep()
@@ -66,7 +66,7 @@ template <int N>
 static int p1f(const PassArgs &a, float2 *dst, cudaStream_t st)
 {
     if constexpr (N <= 512) {
-        const int tiles = a.n1 * (a.n2 / 32);
+        const int tiles = a.n1 * (a.n2 / (2 * TileCfg<N>::C));
         p1_fwd<N><<<std::min(tiles, Occ0<N>::p1), TileCfg<N>::THREADS, smem_p1<N>(), st>>>(a, dst);
     } else {
         using C = ColCfg<N>;
@@ -89,7 +89,7 @@ template <int N>
 static int p5f(const PassArgs &a, cudaStream_t st)
 {
     if constexpr (N <= 512) {
-        const int tiles = a.n1 * (a.n2 / 16);
+        const int tiles = a.n1 * (a.n2 / TileCfg<N>::C);
         p5_fwd<N><<<std::min(tiles, Occ0<N>::p5), TileCfg<N>::THREADS, smem_p5<N>(), st>>>(a);
     } else {
         using C = ColCfg<N>;

@@ -24,9 +24,9 @@ struct Occ1 {
 };
 
 template <int N>
-static constexpr size_t smem_p2() { return (size_t)(N / 2 * 16 + TileCfg<N>::EX) * sizeof(float2); }
+static constexpr size_t smem_p2() { return (size_t)(N / 2 * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 template <int N>
-static constexpr size_t smem_p4() { return (size_t)(2 * N * 16 + TileCfg<N>::EX) * sizeof(float2); }
+static constexpr size_t smem_p4() { return (size_t)(2 * N * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 
 template <int N>
 static int prep()
@@ -65,7 +65,7 @@ template <int N>
 static int p2f(const PassArgs &a, const float2 *src, float2 *dst, cudaStream_t st)
 {
     if constexpr (N <= 512) {
-        const int tiles = (a.n0 + 1) * (a.n2 / 16);
+        const int tiles = (a.n0 + 1) * (a.n2 / TileCfg<N>::C);
         p2_fwd<N><<<std::min(tiles, Occ1<N>::p2), TileCfg<N>::THREADS, smem_p2<N>(), st>>>(a, src, dst);
     } else {
         using C = ColCfg<N>;
@@ -88,7 +88,7 @@ template <int N>
 static int p4f(const PassArgs &a, int withE, cudaStream_t st)
 {
     if constexpr (N <= 512) {
-        const int tiles = (a.n0 + 1) * (a.n2 / 16);
+        const int tiles = (a.n0 + 1) * (a.n2 / TileCfg<N>::C);
         p4_fwd<N><<<std::min(tiles, Occ1<N>::p4), TileCfg<N>::THREADS, smem_p4<N>(), st>>>(a, withE);
     } else {
         using C = ColCfg<N>;

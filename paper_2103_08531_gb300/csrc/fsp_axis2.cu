@@ -86,6 +86,17 @@ static int p3a(const PassArgs &a, int hasE, cudaStream_t st)
     return (int)cudaGetLastError();
 }
 
+int make_twiddles_aux(float2 *tw, int N, cudaStream_t st)
+{
+    switch (N) {
+#define X(n) \
+    case n: k_twiddles_aux<n, typename Plan16<n>::R><<<4, 256, 0, st>>>(tw); return (int)cudaGetLastError();
+        X(64) X(128) X(192) X(256) X(512)
+#undef X
+    default: return 0;   // block-mode lengths use the main table only
+    }
+}
+
 int launch_p3_fwd(int N, const PassArgs &a, int withE, cudaStream_t st)
 {
     switch (N) {

@@ -154,6 +154,40 @@ __device__ __forceinline__ void dft16(float2 *v)
     }
 }
 
+// exp(-/+ 2 pi i u / 32), u = 1..15
+template <bool INV>
+__device__ __forceinline__ float2 w32(float2 a, int u)
+{
+    // cos and sin of u pi / 16
+    const float c[9] = {1.0f, 0.98078528040323044f, 0.92387953251128674f, 0.83146961230254524f,
+                        0.70710678118654752f, 0.55557023301960218f, 0.38268343236508977f, 0.19509032201612827f, 0.0f};
+    if (u == 8) return rot<INV>(a);
+    if (u % 2 == 0) return w16<INV>(a, u / 2);
+    const float cs = u < 8 ? c[u] : -c[16 - u];
+    const float sn = u < 8 ? c[8 - u] : c[u - 8];
+    return cmul_dir<INV>(a, make_float2(cs, -sn));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 *v)
+{
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft16<INV>(e);
+    dft16<INV>(o);
+#pragma unroll
+    for (int u = 1; u < 16; ++u) o[u] = w32<INV>(o[u], u);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        v[u] = e[u] + o[u];
+        v[u + 16] = e[u] - o[u];
+    }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 *v)
 {
@@ -162,6 +196,7 @@ __device__ __forceinline__ void dft(float2 *v)
     else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 8) dft8<INV>(v);
     else if constexpr (R == 16) dft16<INV>(v);
+    else if constexpr (R == 32) dft32<INV>(v);
     else static_assert(R == 2, "unsupported radix");
 }
 
@@ -203,6 +238,20 @@ __device__ __forceinline__ void dft_half_in(float2 *v)
         dft8<INV>(b);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
+            v[2 * u] = a[u];
+            v[2 * u + 1] = b[u];
+        }
+    } else if constexpr (R == 32) {
+        float2 a[16], b[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            a[r] = v[r];
+            b[r] = (r == 0) ? v[0] : w32<INV>(v[r], r);
+        }
+        dft16<INV>(a);
+        dft16<INV>(b);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
             v[2 * u] = a[u];
             v[2 * u + 1] = b[u];
         }
@@ -248,7 +297,10 @@ enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // Twiddle sources: TW_TABLE loads each W^(r m) from the table (cheap when the
 // lanes of a warp share m, as in column tiles); TW_POW loads W^m, W^2m, W^4m,
 // W^8m and forms the other powers by products (lanes with distinct m).
-enum { TW_TABLE = 0, TW_POW = 1 };
+// TW_GATHER (lanes own consecutive j): passes with NS < 32 read a small table
+// laid out [r][k] after the main one (tw + N + OFF), so a warp's loads are
+// contiguous; later passes read the main table, already contiguous in k.
+enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2 };
 
 template <int SYNC>
 __device__ __forceinline__ void lsync()
@@ -288,19 +340,25 @@ __device__ __forceinline__ void twiddle(float2 *u, const float2 *__restrict__ tw
 template <int... RS>
 struct Radices {};
 
-template <int N, int E, bool INV, int NS, class RAD, int SYNC, int TW>
+template <int N, int E, bool INV, int NS, class RAD, int SYNC, int TW, int OFF = 0>
 struct Passes;
 
-template <int N, int E, bool INV, int NS, int SYNC, int TW>
-struct Passes<N, E, INV, NS, Radices<>, SYNC, TW> {
+template <int N, int E, bool INV, int NS, int SYNC, int TW, int OFF>
+struct Passes<N, E, INV, NS, Radices<>, SYNC, TW, OFF> {
     template <bool PRUNE, class View>
     static __device__ __forceinline__ void run(float2 (&)[E], int, const float2 *__restrict__, const View &)
     {
     }
 };
 
-template <int N, int E, bool INV, int NS, int R, int... RS, int SYNC, int TW>
-struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW> {
+// Offset of the gathered twiddle block of the pass after one with (NS, R).
+template <int NS, int R, int OFF>
+struct NextOff {
+    static constexpr int value = OFF + ((NS > 1 && NS < 32) ? R * NS : 0);
+};
+
+template <int N, int E, bool INV, int NS, int R, int... RS, int SYNC, int TW, int OFF>
+struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
     template <bool PRUNE, class View>
     static __device__ __forceinline__ void run(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
     {
@@ -315,7 +373,14 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW> {
             float2 u[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) u[r] = v[q + r * Q];
-            if constexpr (NS > 1) twiddle<R, INV, TW>(u, tw, k * (N / (NS * R)));
+            if constexpr (NS > 1) {
+                if constexpr (TW == TW_GATHER && NS < 32) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + N + OFF + r * NS + k));
+                } else {
+                    twiddle<R, INV, TW == TW_GATHER ? TW_TABLE : TW>(u, tw, k * (N / (NS * R)));
+                }
+            }
             if constexpr (PRUNE && NS == 1) dft_half_in<R, INV>(u);
             else dft<R, INV>(u);
             if constexpr (LAST) {
@@ -332,7 +397,8 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW> {
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = sm.at(j + r * T);
             lsync<SYNC>();
-            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW>::template run<false>(v, j, tw, sm);
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOff<NS, R, OFF>::value>::template run<false>(v, j, tw,
+                                                                                                         sm);
         }
     }
 };
@@ -344,6 +410,34 @@ template <int N, int E, bool INV, bool PRUNE_IN, class RAD, class View, int SYNC
 __device__ __forceinline__ void line_fft(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
 {
     Passes<N, E, INV, 1, RAD, SYNC, TW>::template run<PRUNE_IN>(v, j, tw, sm);
+}
+
+// Gathered twiddle blocks for a radix plan: for every pass with 1 < NS < 32,
+// entry [r][k] (r < R, k < NS) = W_N^(r k N / (NS R)), FP64 angle rounded once.
+template <int N, int NS, int OFF, class RAD>
+struct AuxFill {
+    static __device__ void run(float2 *, int) {}
+};
+template <int N, int NS, int OFF, int R, int... RS>
+struct AuxFill<N, NS, OFF, Radices<R, RS...>> {
+    static __device__ void run(float2 *aux, int i)
+    {
+        if constexpr (NS > 1 && NS < 32) {
+            if (i < R * NS) {
+                const int r = i / NS, k = i % NS;
+                const long long e = (long long)r * k * (N / (NS * R));
+                double sn, cs;
+                sincospi(2.0 * (double)(e % N) / (double)N, &sn, &cs);
+                aux[OFF + i] = make_float2((float)cs, (float)-sn);
+            }
+        }
+        AuxFill<N, NS * R, NextOff<NS, R, OFF>::value, Radices<RS...>>::run(aux, i);
+    }
+};
+template <int N, class RAD>
+__global__ void k_twiddles_aux(float2 *tw)
+{
+    AuxFill<N, 1, 0, RAD>::run(tw + N, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Radix plans per padded length for block-synchronous tiles (E values per thread).
@@ -368,5 +462,10 @@ template <> struct Plan16<128> { static constexpr int E = 16; using R = Radices<
 template <> struct Plan16<192> { static constexpr int E = 12; using R = Radices<4, 4, 4, 3>; };
 template <> struct Plan16<256> { static constexpr int E = 16; using R = Radices<16, 16>; };
 template <> struct Plan16<512> { static constexpr int E = 16; using R = Radices<16, 16, 2>; };
+
+// 32 values per thread: one shared-memory exchange per 512-point transform.
+template <int N>
+struct Plan32 : Plan16<N> {};
+template <> struct Plan32<512> { static constexpr int E = 32; using R = Radices<32, 16>; };
 
 } // namespace fsp

@@ -36,6 +36,8 @@ struct Plan {
 
 // fsp_precompute.cu
 int make_twiddles(float2 *tw, int N, cudaStream_t st);
+int make_twiddles_aux(float2 *tw, int N, cudaStream_t st);   // fsp_axis2.cu
+constexpr int TW_AUX = 1024;   // gathered-twiddle entries after each N-entry table
 int build_kernel_spectrum(Plan *p, cudaStream_t st);
 
 // launchers (return 0 or a cudaError_t value)

@@ -24,6 +24,7 @@
 
 #include "fsp_fft.cuh"
 #include <stdint.h>
+#include <type_traits>
 
 namespace fsp {
 
@@ -505,24 +506,43 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(PassArgs a)
 // while the current one is transformed, so loads overlap the arithmetic.
 // =====================================================================
 
-template <int N>
-struct TileCfg {
+#ifndef FSP_TILE_E
+#define FSP_TILE_E 16
+#endif
+#ifndef FSP_TILE_C
+#define FSP_TILE_C 16
+#endif
+template <int N, int EE>
+struct TilePlan {
     static constexpr int E = Plan16<N>::E;
-    static constexpr int T = N / E;
-    static constexpr int C = 16;
-    static constexpr int THREADS = T * C;
-    using RAD = typename Plan16<N>::R;
-    static constexpr int EX = N * C;   // exchange buffer, float2
+    using R = typename Plan16<N>::R;
+};
+template <int N>
+struct TilePlan<N, 8> {
+    static constexpr int E = Plan1D<N>::E;
+    using R = typename Plan1D<N>::R;
 };
 
-// Rows [0, nrows) of 128 B each (16 complex or 32 real) into dst (row r at dst + 16 r).
+template <int N>
+struct TileCfg {
+    static constexpr int E = TilePlan<N, FSP_TILE_E>::E;
+    static constexpr int T = N / E;
+    static constexpr int C = FSP_TILE_C;           // columns per tile (complex)
+    static constexpr int THREADS = T * C;
+    using RAD = typename TilePlan<N, FSP_TILE_E>::R;
+    static constexpr int EX = N * C;                // exchange buffer, float2
+};
+
+// Rows [0, nrows) of C complex (8 C bytes) each into dst (row r at dst + C r).
+template <int C>
 __device__ __forceinline__ void issue_rows(float2 *dst, const void *src, size_t row_bytes_stride, int nrows, int tid,
                                            int nthr)
 {
+    constexpr int CH = C / 2;   // 16-byte chunks per row
     const char *s = reinterpret_cast<const char *>(src);
-    for (int c = tid; c < nrows * 8; c += nthr) {
-        const int r = c >> 3, part = c & 7;
-        cp_async16(dst + r * 16 + part * 2, s + (size_t)r * row_bytes_stride + part * 16);
+    for (int c = tid; c < nrows * CH; c += nthr) {
+        const int r = c / CH, part = c % CH;
+        cp_async16(dst + r * C + part * 2, s + (size_t)r * row_bytes_stride + part * 16);
     }
 }
 
@@ -531,28 +551,29 @@ template <int N>
 __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(PassArgs a, float2 *__restrict__ dst)
 {
     using C = TileCfg<N>;
+    constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
-    float2 *stage = smem, *ex = smem + NH * 16;
-    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 32, ntiles = a.n1 * zt;
+    float2 *stage = smem, *ex = smem + NH * CC;
+    const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
+    const int zt = a.n2 / (2 * CC), ntiles = a.n1 * zt;
     const size_t rstride = (size_t)a.n1 * a.n2 * sizeof(float);
     auto issue = [&](int t) {
-        const int y = t / zt, z0 = (t % zt) * 32;
-        issue_rows(stage, a.in[0] + gidx(a, 0, y, z0), rstride, NH, tid, C::THREADS);
+        const int y = t / zt, z0 = (t % zt) * (2 * CC);
+        issue_rows<CC>(stage, a.in[0] + gidx(a, 0, y, z0), rstride, NH, tid, C::THREADS);
     };
     int t = blockIdx.x;
     if (t < ntiles) issue(t);
     cp_async_commit();
-    ColView sm{ex + col, 16};
+    ColView sm{ex + col, CC};
     for (; t < ntiles; t += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int y = t / zt, z0 = (t % zt) * 32 + 2 * col;
+        const int y = t / zt, z0 = (t % zt) * (2 * CC) + 2 * col;
         float2 v[E];
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * 16 + col] : make_float2(0.f, 0.f);
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
         __syncthreads();
         if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
         cp_async_commit();
@@ -584,28 +605,29 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(PassArgs a, const 
                                                               float2 *__restrict__ dst)
 {
     using C = TileCfg<N>;
+    constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
-    float2 *stage = smem, *ex = smem + NH * 16;
-    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 16, ntiles = (a.n0 + 1) * zt;
+    float2 *stage = smem, *ex = smem + NH * CC;
+    const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
+    const int zt = a.n2 / CC, ntiles = (a.n0 + 1) * zt;
     const size_t rstride = (size_t)a.n2 * sizeof(float2);
     auto issue = [&](int t) {
-        const int kx = t / zt, z0 = (t % zt) * 16;
-        issue_rows(stage, src + iidx(a, kx, 0, z0), rstride, NH, tid, C::THREADS);
+        const int kx = t / zt, z0 = (t % zt) * CC;
+        issue_rows<CC>(stage, src + iidx(a, kx, 0, z0), rstride, NH, tid, C::THREADS);
     };
     int t = blockIdx.x;
     if (t < ntiles) issue(t);
     cp_async_commit();
-    ColView sm{ex + col, 16};
+    ColView sm{ex + col, CC};
     for (; t < ntiles; t += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int kx = t / zt, z = (t % zt) * 16 + col;
+        const int kx = t / zt, z = (t % zt) * CC + col;
         float2 v[E];
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * 16 + col] : make_float2(0.f, 0.f);
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
         __syncthreads();
         if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
         cp_async_commit();
@@ -622,31 +644,32 @@ template <int N>
 __global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(PassArgs a, int withE)
 {
     using C = TileCfg<N>;
+    constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
-    float2 *st0 = smem, *st1 = smem + N * 16, *ex = smem + 2 * N * 16;
-    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int n1 = a.n1, zt = a.n2 / 16, ntiles = (a.n0 + 1) * zt;
+    float2 *st0 = smem, *st1 = smem + N * CC, *ex = smem + 2 * N * CC;
+    const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
+    const int n1 = a.n1, zt = a.n2 / CC, ntiles = (a.n0 + 1) * zt;
     const size_t rstride = (size_t)a.n2 * sizeof(float2);
     auto issue = [&](int t) {
-        const int kx = t / zt, z0 = (t % zt) * 16;
-        issue_rows(st0, a.buf0 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
-        if (withE) issue_rows(st1, a.buf1 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
+        const int kx = t / zt, z0 = (t % zt) * CC;
+        issue_rows<CC>(st0, a.buf0 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
+        if (withE) issue_rows<CC>(st1, a.buf1 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
     };
     int t = blockIdx.x;
     if (t < ntiles) issue(t);
     cp_async_commit();
-    ColView sm{ex + col, 16};
+    ColView sm{ex + col, CC};
     for (; t < ntiles; t += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int kx = t / zt, z = (t % zt) * 16 + col;
+        const int kx = t / zt, z = (t % zt) * CC + col;
         float2 v[E], w[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            v[r] = st0[(j + r * T) * 16 + col];
-            w[r] = withE ? st1[(j + r * T) * 16 + col] : make_float2(0.f, 0.f);
+            v[r] = st0[(j + r * T) * CC + col];
+            w[r] = withE ? st1[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
@@ -676,45 +699,46 @@ template <int N>
 __global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
 {
     using C = TileCfg<N>;
+    constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T, NH = N / 2, ROWS = N / 2 + 1;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
-    float2 *sA = smem, *sB = smem + ROWS * 16, *sC = smem + 2 * ROWS * 16, *ex = smem + 3 * ROWS * 16;
+    float2 *sA = smem, *sB = smem + ROWS * CC, *sC = smem + 2 * ROWS * CC, *ex = smem + 3 * ROWS * CC;
     float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
     const bool first = phi || e0, second = e1 != nullptr;
-    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 16, ntiles = a.n1 * zt;
+    const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
+    const int zt = a.n2 / CC, ntiles = a.n1 * zt;
     const size_t rstride = (size_t)a.rows1 * a.n2 * sizeof(float2);
     auto issue = [&](int t) {
-        const int y = t / zt, z0 = (t % zt) * 16;
-        if (first) issue_rows(sA, a.buf0 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+        const int y = t / zt, z0 = (t % zt) * CC;
+        if (first) issue_rows<CC>(sA, a.buf0 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
         if (second) {
             if (a.three_d) {
-                issue_rows(sB, a.buf0 + iidx(a, 0, a.n1 + y, z0), rstride, ROWS, tid, C::THREADS);
-                issue_rows(sC, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+                issue_rows<CC>(sB, a.buf0 + iidx(a, 0, a.n1 + y, z0), rstride, ROWS, tid, C::THREADS);
+                issue_rows<CC>(sC, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
             } else {
-                issue_rows(sB, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+                issue_rows<CC>(sB, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
             }
         }
     };
     int t = blockIdx.x;
     if (t < ntiles) issue(t);
     cp_async_commit();
-    ColView sm{ex + col, 16};
+    ColView sm{ex + col, CC};
     for (; t < ntiles; t += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int y = t / zt, z = (t % zt) * 16 + col;
+        const int y = t / zt, z = (t % zt) * CC + col;
         float2 v[E], w[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int k = j + r * T;
             const int src = k <= NH ? k : N - k;
             float2 p = make_float2(0.f, 0.f), Y = p, Z = p;
-            if (first) p = sA[src * 16 + col];
+            if (first) p = sA[src * CC + col];
             if (second) {
-                Y = sB[src * 16 + col];
-                if (a.three_d) Z = sC[src * 16 + col];
+                Y = sB[src * CC + col];
+                if (a.three_d) Z = sC[src * CC + col];
             }
             if (k > NH) {
                 p.y = -p.y;
@@ -752,23 +776,43 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
 
 // ------------------------------------------------- warp-per-line middle pass
 
+#ifndef FSP_P3_TW
+#define FSP_P3_TW TW_POW
+#endif
+
+#ifndef FSP_P3_E32
+#define FSP_P3_E32 0
+#endif
+#ifndef FSP_P3_SAVE
+#define FSP_P3_SAVE 0
+#endif
+#ifndef FSP_P3_PREFETCH
+#define FSP_P3_PREFETCH 1
+#endif
+#ifndef FSP_P3_MINB
+#define FSP_P3_MINB 1
+#endif
+template <int N>
+using P3Plan = typename std::conditional<FSP_P3_E32 != 0, Plan32<N>, Plan16<N>>::type;
+
 template <int N>
 struct WarpCfg {
-    static constexpr int E = Plan16<N>::E;
+    static constexpr int E = P3Plan<N>::E;
     static constexpr int T = N / E;
     static constexpr int LPW = 32 / T;     // lines per warp
     static constexpr int WARPS = 4;
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int PAD = 4;
     static constexpr int SPAN = RowSpan<N, PAD>::value;
-    using RAD = typename Plan16<N>::R;
-    static constexpr size_t SMEM = (size_t)SPAN * LPW * WARPS * sizeof(float2);
+    using RAD = typename P3Plan<N>::R;
+    static constexpr int SAVE = FSP_P3_SAVE;    // keep the product spectrum in shared memory, not registers
+    static constexpr size_t SMEM = (size_t)(SPAN + (SAVE ? N : 0)) * LPW * WARPS * sizeof(float2);
 };
 
 // Forward middle pass, one warp per line (or per 32/T lines), persistent over
 // lines with the next line's input prefetched into registers.
 template <int N>
-__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd(PassArgs a, int withE)
+__global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(PassArgs a, int withE)
 {
     using C = WarpCfg<N>;
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
@@ -783,7 +827,7 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd(PassArgs a, int wi
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
     int g = blockIdx.x * C::WARPS + warp;
     float2 pv[E / 2];
-    {
+    if (FSP_P3_PREFETCH) {
         const int line = g * LPW + li;
         const bool act = g < groups && line < lines;
         const float2 *L = a.buf0 + (size_t)(act ? line : 0) * n2;
@@ -795,9 +839,14 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd(PassArgs a, int wi
         const bool act = line < lines;
         const int lc = act ? line : 0;
         float2 v[E];
+        if (!FSP_P3_PREFETCH) {
+            const float2 *L = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
-        {
+        if (FSP_P3_PREFETCH) {
             const int ng = g + gstride;
             const int nline = ng * LPW + li;
             const bool nact = ng < groups && nline < lines;
@@ -807,29 +856,61 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd(PassArgs a, int wi
                 if (nact) pv[r] = L[j + r * T];
         }
         const int kx = lc / a.rows1, row = lc % a.rows1;
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
         const float *Kr = krow(a, kx, row);
-        float2 u[E];
+        if constexpr (C::SAVE) {
+            float2 *sv = smem + C::SPAN * LPW * C::WARPS + (size_t)(warp * LPW + li) * N;
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int k = j + r * T;
-            const int kf = k <= n2 ? k : N - k;
-            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
-            const float kk = wave(k, n2, a.k2s);
-            u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
-        }
-        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
-        if (act) {
-            float2 *L0 = a.buf0 + (size_t)lc * n2;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
-        }
-        if (withE) {
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(u, j, a.tw2, sm);
+            for (int r = 0; r < E; ++r) {
+                const int k = j + r * T;
+                const int kf = k <= n2 ? k : N - k;
+                v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+                if (withE) sv[k] = v[r];
+            }
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
             if (act) {
-                float2 *L1 = a.buf1 + (size_t)lc * n2;
+                float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
-                for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
+                for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+            }
+            if (withE) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int k = j + r * T;
+                    const float kk = wave(k, n2, a.k2s);
+                    const float2 sk = sv[k];
+                    v[r] = make_float2(kk * sk.y, -kk * sk.x);
+                }
+                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+                if (act) {
+                    float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                    for (int r = 0; r < E / 2; ++r) L1[j + r * T] = v[r];
+                }
+            }
+        } else {
+            float2 u[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int k = j + r * T;
+                const int kf = k <= n2 ? k : N - k;
+                v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+                const float kk = wave(k, n2, a.k2s);
+                u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+            }
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+            if (act) {
+                float2 *L0 = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+                for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+            }
+            if (withE) {
+                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, a.tw2, sm);
+                if (act) {
+                    float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                    for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
+                }
             }
         }
     }
@@ -858,12 +939,12 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(PassArgs a, int ha
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = (r < E / 2 && act) ? L0[j + r * T] : make_float2(0.f, 0.f);
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
         if (hasE) {
             float2 w[E];
 #pragma unroll
             for (int r = 0; r < E; ++r) w[r] = (r < E / 2 && act) ? L1[j + r * T] : make_float2(0.f, 0.f);
-            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(w, j, a.tw2, sm);
+            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(w, j, a.tw2, sm);
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const float kk = wave(j + r * T, n2, a.k2s);
@@ -878,7 +959,7 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(PassArgs a, int ha
             const int kf = k <= n2 ? k : N - k;
             v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
         }
-        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_POW>(v, j, a.tw2, sm);
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
         if (act) {
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
