@@ -363,6 +363,113 @@ def run_gpu(args):
     return 0
 
 
+# ----------------------------------------------------------- other workloads
+
+def pass_bytes_2d(shape, with_E=True):
+    """Algorithmic bytes of the 2D pipeline (P1 axis 0 R2C, P3 fused along axis 1, P5 C2R)."""
+    n0, n2 = shape
+    cells = n0 * n2
+    S = (n0 + 1) * n2
+    K = 4 * (n0 + 1) * (n2 + 1)
+    s3, outs = (2, 3) if with_E else (1, 1)
+    return {"p1_fwd": 4 * cells + 8 * S, "p3_fwd": 8 * S + K + s3 * 8 * S, "p5_fwd": s3 * 8 * S + 4 * outs * cells}
+
+
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_other(args):
+    """Single-GPU measurements of the other workloads (one JSON line each)."""
+    import torch
+    import paper_2103_08531_gb300 as fsp
+    from paper_2103_08531_gb300 import build
+    build.build()
+    peak, peak_kind = measured_peaks()
+    clocks = ClockSampler(0)
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    if args.workload == "beam64":
+        probs = W.beam_batch(64, seed=3)
+        t = time.perf_counter()
+        plans = [fsp.Plan(p.shape, p.h, "vgf") for p in probs]
+        t_plan = time.perf_counter() - t
+        rhos = [torch.from_numpy(p.rho(np.float32)).cuda() for p in probs]
+        batch = fsp.Batch(plans, rhos)
+        graph = batch.capture()
+        clocks.start()
+        ms = _timed(graph.replay, args.steps, args.warmup)
+        ms_seq = _timed(lambda: [pl.solve(r, phi=ph, E=e) for pl, r, ph, e in
+                                 zip(plans, rhos, batch.phis, batch.Es)], args.steps, args.warmup)
+        clk = clocks.stop()
+        pts = sum(p.points for p in probs)
+        byts = sum(sum(pass_bytes(p.shape, True).values()) for p in probs)
+        per = ms / args.steps
+        line.update({"metric": "batched VGF solves/s, 64 uneven beam-bunch geometries, one graph replay per batch",
+                     "value": 64 / (per * 1e-3), "unit": "solves/s", "ms_per_step": per,
+                     "config": {"workload": "64 x 3D VGF, shapes from {64^3,96^3,128^3,64x64x256,128x128x512}, "
+                                            "h_a U[0.005,0.03], one Gaussian each (seed 3), phi+E, CUDA graph"},
+                     "gpts_per_s": pts / (per * 1e-3) / 1e9,
+                     "pipeline": {"bytes": byts, "gbs": byts / (per * 1e-3) / 1e9,
+                                  "frac": byts / (per * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
+                     "sequential_ms_per_batch": ms_seq / args.steps, "plan_seconds_64_geometries": t_plan,
+                     "gpu_launches": None, "clocks": clk})
+    elif args.workload == "gauss2d4096":
+        prob = W.mixture_2d(4096, 16, 2)
+        rho = torch.from_numpy(prob.rho(np.float32)).cuda()
+        res = {}
+        clocks.start()
+        for m in ("vgf", "he"):
+            plan = fsp.Plan(prob.shape, prob.h, m)
+            phi = torch.empty_like(rho)
+            E = torch.empty((2,) + prob.shape, device="cuda")
+            res[m] = _timed(lambda: plan.solve(rho, phi=phi, E=E), args.steps, args.warmup) / args.steps
+        clk = clocks.stop()
+        byts = sum(pass_bytes_2d(prob.shape).values())
+        per = res["vgf"]
+        line.update({"metric": "2D VGF solves/s at 4096^2 FP32 (phi+E)", "value": 1e3 / per, "unit": "solves/s",
+                     "ms_per_step": per, "config": {"workload": "2D VGF 4096^2 on [-1,1]^2, 16 Gaussians (seed 2)"},
+                     "gpts_per_s": prob.points / (per * 1e-3) / 1e9, "he_ms_per_step": res["he"],
+                     "pipeline": {"bytes": byts, "gbs": byts / (per * 1e-3) / 1e9,
+                                  "frac": byts / (per * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
+                     "gpu_launches": 3 * args.steps, "clocks": clk})
+    elif args.workload == "train128":
+        n, B = 128, 8
+        probs, target = W.training_batch(n, B)
+        plan = fsp.Plan((n, n, n), probs[0].h, "vgf")
+        tgt = torch.from_numpy(target).cuda()
+        rhos = [torch.from_numpy(p.rho(np.float32)).cuda().requires_grad_(True) for p in probs]
+
+        def step():
+            loss = 0.0
+            for r in rhos:
+                r.grad = None
+                phi, E = fsp.FspSolve.apply(r, plan)
+                loss = loss + ((phi - tgt) ** 2).sum() + 0.1 * (E ** 2).sum()
+            loss.backward()
+
+        clocks.start()
+        per = _timed(step, args.steps, args.warmup) / args.steps
+        clk = clocks.stop()
+        line.update({"metric": "differentiable VGF: forward + adjoint per batch of 8 at 128^3 (loss on phi and E)",
+                     "value": B / (per * 1e-3), "unit": "fwd+bwd items/s", "ms_per_step": per,
+                     "config": {"workload": "8 x 128^3 VGF, 4-Gaussian densities (seeds 10..17), "
+                                            "loss sum (phi - phi_t)^2 + 0.1 |E|^2"},
+                     "gpu_launches": None, "clocks": clk})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,11 +478,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["vgf256", "beam64", "gauss2d4096", "train128"], default="vgf256",
+                    help="vgf256 is the headline; the others print their own line (1 GPU)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "vgf256":
+        return run_other(args)
     return run_gpu(args)
 
 

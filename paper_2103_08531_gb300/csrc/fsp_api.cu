@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -312,8 +313,7 @@ static inline void mark(const Plan &p, int i, cudaStream_t st)
     if (p.n_pass_ev > i) cudaEventRecord(p.pass_ev[i], st);
 }
 
-// Forward pipeline for one plan on its workspace `ws`.
-int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
+static PassArgs fwd_args(const Plan &p, void *ws, const float *rho, float *phi, float *E)
 {
     PassArgs a = base_args(p, ws);
     const size_t c = cells(p);
@@ -324,29 +324,31 @@ int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E,
         a.out[2] = E + c;
         a.out[3] = p.three_d ? E + 2 * c : nullptr;
     }
+    return a;
+}
+
+// Forward pipeline for one plan on its workspace `ws`.
+int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
+{
+    PassArgs a = fwd_args(p, ws, rho, phi, E);
     const int withE = E != nullptr;
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
-    int e = 0;
-    mark(p, 0, st);
-    if (p.three_d) {
-        e = launch_p1_fwd(N0, a, a.buf1, st);
-        mark(p, 1, st);
-        if (!e) e = launch_p2_fwd(N1, a, a.buf1, a.buf0, st);
-        mark(p, 2, st);
-        if (!e) e = launch_p3_fwd(N2, a, withE, st);
-        mark(p, 3, st);
-        if (!e) e = launch_p4_fwd(N1, a, withE, st);
-        mark(p, 4, st);
-        if (!e) e = launch_p5_fwd(N0, a, st);
-        mark(p, 5, st);
-    } else {
-        e = launch_p1_fwd(N0, a, a.buf0, st);
-        mark(p, 1, st);
-        if (!e) e = launch_p3_fwd(N2, a, withE, st);
-        mark(p, 2, st);
-        if (!e) e = launch_p5_fwd(N0, a, st);
-        mark(p, 3, st);
+    int e = 0, m = 0;
+    mark(p, m++, st);
+    e = launch_axis0(PASS_P1F, N0, &a, 1, st);
+    mark(p, m++, st);
+    if (!e && p.three_d) {
+        e = launch_axis1(PASS_P2F, N1, &a, 1, 0, st);
+        mark(p, m++, st);
     }
+    if (!e) e = launch_axis2(PASS_P3F, N2, &a, 1, withE, st);
+    mark(p, m++, st);
+    if (!e && p.three_d) {
+        e = launch_axis1(PASS_P4F, N1, &a, 1, withE, st);
+        mark(p, m++, st);
+    }
+    if (!e) e = launch_axis0(PASS_P5F, N0, &a, 1, st);
+    mark(p, m++, st);
     return e ? FSP_ERR_CUDA : FSP_OK;
 }
 
@@ -362,26 +364,80 @@ int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, f
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
     int m = 0;
     mark(p, m++, st);
-    int e = launch_p1_adj(N0, a, st);
+    int e = launch_axis0(PASS_P1A, N0, &a, 1, st);
     mark(p, m++, st);
     if (!e && p.three_d) {
-        e = launch_p2_adj(N1, a, 1, st);
+        e = launch_axis1(PASS_P2A, N1, &a, 1, 1, st);
         mark(p, m++, st);
     }
-    if (!e) e = launch_p3_adj(N2, a, 1, st);
+    if (!e) e = launch_axis2(PASS_P3A, N2, &a, 1, 1, st);
     mark(p, m++, st);
     if (!e && p.three_d) {
-        e = launch_p4_fwd(N1, a, 0, st);
+        e = launch_axis1(PASS_P4F, N1, &a, 1, 0, st);
         mark(p, m++, st);
     }
     if (!e) {
         PassArgs b = a;
         b.out[0] = g_rho;
         b.out[1] = b.out[2] = b.out[3] = nullptr;
-        e = launch_p5_fwd(N0, b, st);
+        e = launch_axis0(PASS_P5F, N0, &b, 1, st);
     }
     mark(p, m++, st);
     return e ? FSP_ERR_CUDA : FSP_OK;
+}
+
+// One pass over many items: the items sharing a padded length go in one launch.
+struct PassLaunch {
+    int kind, axis, N, flag;
+    std::vector<PassArgs> items;
+};
+
+static void group_pass(std::vector<PassLaunch> &out, int kind, int axis, int flag, const std::vector<PassArgs> &items,
+                       const std::vector<int> &Ns, const std::vector<int> &use)
+{
+    std::vector<int> seen;
+    for (size_t i = 0; i < items.size(); ++i) {
+        if (!use[i] || std::find(seen.begin(), seen.end(), Ns[i]) != seen.end()) continue;
+        seen.push_back(Ns[i]);
+        PassLaunch L{kind, axis, Ns[i], flag, {}};
+        for (size_t k = i; k < items.size(); ++k)
+            if (use[k] && Ns[k] == Ns[i]) L.items.push_back(items[k]);
+        out.push_back(std::move(L));
+    }
+}
+
+// Launch plan of a forward batch: P1 over all items, then P2 (3D items), P3,
+// P4 (3D items), P5, each split by padded length only.
+static std::vector<PassLaunch> batch_launches(const std::vector<const Plan *> &plans, const std::vector<PassArgs> &items,
+                                              int withE)
+{
+    const size_t n = plans.size();
+    std::vector<int> N0(n), N1(n), N2(n), all(n, 1), is3(n);
+    for (size_t i = 0; i < n; ++i) {
+        N0[i] = 2 * plans[i]->n0;
+        N1[i] = 2 * plans[i]->n1;
+        N2[i] = 2 * plans[i]->n2;
+        is3[i] = plans[i]->three_d;
+    }
+    std::vector<PassLaunch> L;
+    group_pass(L, PASS_P1F, 0, 0, items, N0, all);
+    group_pass(L, PASS_P2F, 1, 0, items, N1, is3);
+    group_pass(L, PASS_P3F, 2, withE, items, N2, all);
+    group_pass(L, PASS_P4F, 1, withE, items, N1, is3);
+    group_pass(L, PASS_P5F, 0, 0, items, N0, all);
+    return L;
+}
+
+static int run_launches(const std::vector<PassLaunch> &L, cudaStream_t st)
+{
+    for (const PassLaunch &x : L) {
+        const int n = (int)x.items.size();
+        int e = x.axis == 0 ? launch_axis0(x.kind, x.N, x.items.data(), n, st)
+                : x.axis == 1 ? launch_axis1(x.kind, x.N, x.items.data(), n, x.flag, st)
+                              : launch_axis2(x.kind, x.N, x.items.data(), n, x.flag, st);
+        if (e) return FSP_ERR_CUDA;
+    }
+    return FSP_OK;
 }
 
 } // namespace fsp
@@ -408,9 +464,7 @@ extern "C" int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *
 // ----------------------------------------------------------------- batches
 
 struct fsp_batch {
-    std::vector<fsp_plan *> plans;
-    std::vector<const float *> rho;
-    std::vector<float *> phi, E;
+    std::vector<PassLaunch> launches;
 };
 
 static int check_batch(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi, void *const *E)
@@ -419,6 +473,7 @@ static int check_batch(fsp_plan *const *plans, int count, const void *const *rho
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !rho[i] || !aligned16(rho[i])) return FSP_ERR_INVALID;
         if (!(phi && phi[i]) && !(E && E[i])) return FSP_ERR_INVALID;
+        if (E && !E[i]) return FSP_ERR_INVALID;   // with_E must hold for every item
         if ((phi && phi[i] && !aligned16(phi[i])) || (E && E[i] && !aligned16(E[i]))) return FSP_ERR_INVALID;
         const Plan &p = plans[i]->p;
         if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return FSP_ERR_WORKSPACE;
@@ -428,15 +483,26 @@ static int check_batch(fsp_plan *const *plans, int count, const void *const *rho
     return FSP_OK;
 }
 
+static std::vector<PassLaunch> plan_batch(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
+                                          void *const *E)
+{
+    std::vector<const Plan *> ps;
+    std::vector<PassArgs> items;
+    for (int i = 0; i < count; ++i) {
+        const Plan &p = plans[i]->p;
+        ps.push_back(&p);
+        items.push_back(fwd_args(p, p.ws, (const float *)rho[i], phi ? (float *)phi[i] : nullptr,
+                                 E ? (float *)E[i] : nullptr));
+    }
+    return batch_launches(ps, items, E != nullptr);
+}
+
 extern "C" int fsp_solve_batched(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
                                  void *const *E, void *cuda_stream)
 {
     int rc = check_batch(plans, count, rho, phi, E);
     if (rc) return set_err(rc);
-    for (int i = 0; i < count && rc == FSP_OK; ++i)
-        rc = run_forward(plans[i]->p, plans[i]->p.ws, (const float *)rho[i], phi ? (float *)phi[i] : nullptr,
-                         E ? (float *)E[i] : nullptr, (cudaStream_t)cuda_stream);
-    return set_err(rc);
+    return set_err(run_launches(plan_batch(plans, count, rho, phi, E), (cudaStream_t)cuda_stream));
 }
 
 extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
@@ -452,12 +518,7 @@ extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const 
         set_err(FSP_ERR_NOMEM);
         return nullptr;
     }
-    for (int i = 0; i < count; ++i) {
-        b->plans.push_back(plans[i]);
-        b->rho.push_back((const float *)rho[i]);
-        b->phi.push_back(phi ? (float *)phi[i] : nullptr);
-        b->E.push_back(E ? (float *)E[i] : nullptr);
-    }
+    b->launches = plan_batch(plans, count, rho, phi, E);
     set_err(FSP_OK);
     return b;
 }
@@ -465,10 +526,7 @@ extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const 
 extern "C" int fsp_batch_solve(fsp_batch *b, void *cuda_stream)
 {
     if (!b) return set_err(FSP_ERR_INVALID);
-    int rc = FSP_OK;
-    for (size_t i = 0; i < b->plans.size() && rc == FSP_OK; ++i)
-        rc = run_forward(b->plans[i]->p, b->plans[i]->p.ws, b->rho[i], b->phi[i], b->E[i], (cudaStream_t)cuda_stream);
-    return set_err(rc);
+    return set_err(run_launches(b->launches, (cudaStream_t)cuda_stream));
 }
 
 extern "C" void fsp_batch_destroy(fsp_batch *b) { delete b; }

@@ -3,10 +3,56 @@
 #include "fsp_passes.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace fsp {
 
 #define FSP_AXIS0_SIZES(X) X(64) X(128) X(192) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+namespace {
+
+template <int MAXI>
+Work<MAXI> make_work(const PassArgs *items, int n, int (*units)(const PassArgs &))
+{
+    Work<MAXI> w;
+    w.nitems = n;
+    w.offs[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        w.item[i] = items[i];
+        w.offs[i + 1] = w.offs[i] + units(items[i]);
+    }
+    return w;
+}
+
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return sms;
+}
+
+// Launch helper: runs `body(work, grid_cap)` over items in chunks of BATCH_MAX.
+template <class F>
+int chunked(const PassArgs *items, int n, int (*units)(const PassArgs &), F body)
+{
+    if (n == 1) {
+        Work<1> w = make_work<1>(items, 1, units);
+        return body(w);
+    }
+    for (int i = 0; i < n; i += BATCH_MAX) {
+        const int m = std::min(BATCH_MAX, n - i);
+        Work<BATCH_MAX> w = make_work<BATCH_MAX>(items + i, m, units);
+        int e = body(w);
+        if (e) return e;
+    }
+    return 0;
+}
+
+} // namespace
 
 int supported_axis0(int N)
 {
@@ -18,38 +64,41 @@ int supported_axis0(int N)
     }
 }
 
-// Tile kernels (2n <= 512) are persistent: grid = SMs x resident CTAs per SM.
-template <int N>
-struct Occ0 {
-    static inline int p1 = 0, p5 = 0;
-};
-
 template <int N>
 static constexpr size_t smem_p1() { return (size_t)(N / 2 * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 template <int N>
 static constexpr size_t smem_p5() { return (size_t)(3 * (N / 2 + 1) * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 
+// resident CTAs per SM of the persistent kernels (set by prepare)
+template <int N, int MAXI>
+struct Occ0 {
+    static inline int p1 = 1, p5 = 1;
+};
+
+template <int N, int MAXI>
+static int prep_one()
+{
+    using C = ColCfg<N>;
+    int e = cudaFuncSetAttribute(p1_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if constexpr (N <= 512) {
+        e |= cudaFuncSetAttribute(p1_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1<N>());
+        e |= cudaFuncSetAttribute(p5_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5<N>());
+        int b1 = 0, b5 = 0;
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p1<N>());
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p5<N>());
+        Occ0<N, MAXI>::p1 = std::max(1, b1);
+        Occ0<N, MAXI>::p5 = std::max(1, b5);
+    } else {
+        e |= cudaFuncSetAttribute(p1_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        e |= cudaFuncSetAttribute(p5_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    }
+    return e;
+}
+
 template <int N>
 static int prep()
 {
-    using C = ColCfg<N>;
-    int e = 0;
-    e |= cudaFuncSetAttribute(p1_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if constexpr (N <= 512) {
-        e |= cudaFuncSetAttribute(p1_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1<N>());
-        e |= cudaFuncSetAttribute(p5_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5<N>());
-        int dev = 0, sms = 0, b1 = 0, b5 = 0;
-        e |= cudaGetDevice(&dev);
-        e |= cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_fwd<N>, TileCfg<N>::THREADS, smem_p1<N>());
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_fwd<N>, TileCfg<N>::THREADS, smem_p5<N>());
-        Occ0<N>::p1 = sms * (b1 > 0 ? b1 : 1);
-        Occ0<N>::p5 = sms * (b5 > 0 ? b5 : 1);
-    } else {
-        e |= cudaFuncSetAttribute(p1_fwd_blk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        e |= cudaFuncSetAttribute(p5_fwd_blk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    }
-    return e;
+    return prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
 }
 
 int prepare_axis0(int N)
@@ -63,66 +112,63 @@ int prepare_axis0(int N)
 }
 
 template <int N>
-static int p1f(const PassArgs &a, float2 *dst, cudaStream_t st)
+static int units_p1f(const PassArgs &a)
 {
-    if constexpr (N <= 512) {
-        const int tiles = a.n1 * (a.n2 / (2 * TileCfg<N>::C));
-        p1_fwd<N><<<std::min(tiles, Occ0<N>::p1), TileCfg<N>::THREADS, smem_p1<N>(), st>>>(a, dst);
-    } else {
-        using C = ColCfg<N>;
-        dim3 grid((a.n2 / 2 + C::BZ - 1) / C::BZ, a.n1);
-        p1_fwd_blk<N><<<grid, C::THREADS, C::SMEM, st>>>(a, dst);
-    }
-    return (int)cudaGetLastError();
+    if constexpr (N <= 512) return a.n1 * (a.n2 / (2 * TileCfg<N>::C));
+    else return a.n1 * ((a.n2 / 2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
+}
+template <int N>
+static int units_col(const PassArgs &a)   // (y, column tile) units of P1-adjoint and the block P5
+{
+    return a.n1 * ((a.n2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
+}
+template <int N>
+static int units_p5f(const PassArgs &a)
+{
+    if constexpr (N <= 512) return a.n1 * (a.n2 / TileCfg<N>::C);
+    else return units_col<N>(a);
 }
 
 template <int N>
-static int p1a(const PassArgs &a, cudaStream_t st)
+static int run(int kind, const PassArgs *items, int n, cudaStream_t st)
 {
-    using C = ColCfg<N>;
-    dim3 grid((a.n2 + C::BZ - 1) / C::BZ, a.n1);
-    p1_adj<N><<<grid, C::THREADS, C::SMEM, st>>>(a);
-    return (int)cudaGetLastError();
-}
-
-template <int N>
-static int p5f(const PassArgs &a, cudaStream_t st)
-{
-    if constexpr (N <= 512) {
-        const int tiles = a.n1 * (a.n2 / TileCfg<N>::C);
-        p5_fwd<N><<<std::min(tiles, Occ0<N>::p5), TileCfg<N>::THREADS, smem_p5<N>(), st>>>(a);
-    } else {
-        using C = ColCfg<N>;
-        dim3 grid((a.n2 + C::BZ - 1) / C::BZ, a.n1);
-        p5_fwd_blk<N><<<grid, C::THREADS, C::SMEM, st>>>(a);
+    const int cap_sm = sm_count();
+    if (kind == PASS_P1F) {
+        return chunked(items, n, units_p1f<N>, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            const int total = w.offs[w.nitems];
+            if constexpr (N <= 512)
+                p1_fwd<N, MAXI><<<std::min(total, cap_sm * Occ0<N, MAXI>::p1), TileCfg<N>::THREADS, smem_p1<N>(), st>>>(w);
+            else
+                p1_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+            return (int)cudaGetLastError();
+        });
     }
-    return (int)cudaGetLastError();
+    if (kind == PASS_P1A) {
+        return chunked(items, n, units_col<N>, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            p1_adj<N, MAXI><<<w.offs[w.nitems], ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+            return (int)cudaGetLastError();
+        });
+    }
+    if (kind == PASS_P5F) {
+        return chunked(items, n, units_p5f<N>, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            const int total = w.offs[w.nitems];
+            if constexpr (N <= 512)
+                p5_fwd<N, MAXI><<<std::min(total, cap_sm * Occ0<N, MAXI>::p5), TileCfg<N>::THREADS, smem_p5<N>(), st>>>(w);
+            else
+                p5_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+            return (int)cudaGetLastError();
+        });
+    }
+    return (int)cudaErrorInvalidValue;
 }
 
-int launch_p1_fwd(int N, const PassArgs &a, float2 *dst, cudaStream_t st)
+int launch_axis0(int kind, int N, const PassArgs *items, int n, cudaStream_t st)
 {
     switch (N) {
-#define X(n) case n: return p1f<n>(a, dst, st);
-        FSP_AXIS0_SIZES(X)
-#undef X
-    default: return (int)cudaErrorInvalidValue;
-    }
-}
-
-int launch_p1_adj(int N, const PassArgs &a, cudaStream_t st)
-{
-    switch (N) {
-#define X(n) case n: return p1a<n>(a, st);
-        FSP_AXIS0_SIZES(X)
-#undef X
-    default: return (int)cudaErrorInvalidValue;
-    }
-}
-
-int launch_p5_fwd(int N, const PassArgs &a, cudaStream_t st)
-{
-    switch (N) {
-#define X(n) case n: return p5f<n>(a, st);
+#define X(v) case v: return run<v>(kind, items, n, st);
         FSP_AXIS0_SIZES(X)
 #undef X
     default: return (int)cudaErrorInvalidValue;

@@ -3,10 +3,56 @@
 #include "fsp_passes.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace fsp {
 
 #define FSP_AXIS1_SIZES(X) X(64) X(128) X(192) X(256) X(512) X(1024)
+
+namespace {
+
+template <int MAXI>
+Work<MAXI> make_work(const PassArgs *items, int n, int (*units)(const PassArgs &))
+{
+    Work<MAXI> w;
+    w.nitems = n;
+    w.offs[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        w.item[i] = items[i];
+        w.offs[i + 1] = w.offs[i] + units(items[i]);
+    }
+    return w;
+}
+
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return sms;
+}
+
+// Launch helper: runs `body(work, grid_cap)` over items in chunks of BATCH_MAX.
+template <class F>
+int chunked(const PassArgs *items, int n, int (*units)(const PassArgs &), F body)
+{
+    if (n == 1) {
+        Work<1> w = make_work<1>(items, 1, units);
+        return body(w);
+    }
+    for (int i = 0; i < n; i += BATCH_MAX) {
+        const int m = std::min(BATCH_MAX, n - i);
+        Work<BATCH_MAX> w = make_work<BATCH_MAX>(items + i, m, units);
+        int e = body(w);
+        if (e) return e;
+    }
+    return 0;
+}
+
+} // namespace
 
 int supported_axis1(int N)
 {
@@ -19,36 +65,39 @@ int supported_axis1(int N)
 }
 
 template <int N>
-struct Occ1 {
-    static inline int p2 = 0, p4 = 0;
-};
-
-template <int N>
 static constexpr size_t smem_p2() { return (size_t)(N / 2 * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 template <int N>
 static constexpr size_t smem_p4() { return (size_t)(2 * N * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
 
+template <int N, int MAXI>
+struct Occ1 {
+    static inline int p2 = 1, p4 = 1;
+};
+
+template <int N, int MAXI>
+static int prep_one()
+{
+    using C = ColCfg<N>;
+    int e = cudaFuncSetAttribute(p2_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if constexpr (N <= 512) {
+        e |= cudaFuncSetAttribute(p2_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2<N>());
+        e |= cudaFuncSetAttribute(p4_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4<N>());
+        int b2 = 0, b4 = 0;
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p2<N>());
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p4<N>());
+        Occ1<N, MAXI>::p2 = std::max(1, b2);
+        Occ1<N, MAXI>::p4 = std::max(1, b4);
+    } else {
+        e |= cudaFuncSetAttribute(p2_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        e |= cudaFuncSetAttribute(p4_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    }
+    return e;
+}
+
 template <int N>
 static int prep()
 {
-    using C = ColCfg<N>;
-    int e = 0;
-    e |= cudaFuncSetAttribute(p2_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if constexpr (N <= 512) {
-        e |= cudaFuncSetAttribute(p2_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2<N>());
-        e |= cudaFuncSetAttribute(p4_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4<N>());
-        int dev = 0, sms = 0, b2 = 0, b4 = 0;
-        e |= cudaGetDevice(&dev);
-        e |= cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_fwd<N>, TileCfg<N>::THREADS, smem_p2<N>());
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_fwd<N>, TileCfg<N>::THREADS, smem_p4<N>());
-        Occ1<N>::p2 = sms * (b2 > 0 ? b2 : 1);
-        Occ1<N>::p4 = sms * (b4 > 0 ? b4 : 1);
-    } else {
-        e |= cudaFuncSetAttribute(p2_fwd_blk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        e |= cudaFuncSetAttribute(p4_fwd_blk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    }
-    return e;
+    return prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
 }
 
 int prepare_axis1(int N)
@@ -62,66 +111,58 @@ int prepare_axis1(int N)
 }
 
 template <int N>
-static int p2f(const PassArgs &a, const float2 *src, float2 *dst, cudaStream_t st)
+static int units_tile(const PassArgs &a)   // (k0, column tile) units
 {
-    if constexpr (N <= 512) {
-        const int tiles = (a.n0 + 1) * (a.n2 / TileCfg<N>::C);
-        p2_fwd<N><<<std::min(tiles, Occ1<N>::p2), TileCfg<N>::THREADS, smem_p2<N>(), st>>>(a, src, dst);
-    } else {
-        using C = ColCfg<N>;
-        dim3 grid((a.n2 + C::BZ - 1) / C::BZ, a.n0 + 1);
-        p2_fwd_blk<N><<<grid, C::THREADS, C::SMEM, st>>>(a, src, dst);
-    }
-    return (int)cudaGetLastError();
+    if constexpr (N <= 512) return (a.n0 + 1) * (a.n2 / TileCfg<N>::C);
+    else return (a.n0 + 1) * ((a.n2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
+}
+template <int N>
+static int units_blk(const PassArgs &a)
+{
+    return (a.n0 + 1) * ((a.n2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
 }
 
 template <int N>
-static int p2a(const PassArgs &a, int hasE, cudaStream_t st)
+static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st)
 {
-    using C = ColCfg<N>;
-    dim3 grid((a.n2 + C::BZ - 1) / C::BZ, a.n0 + 1);
-    p2_adj<N><<<grid, C::THREADS, C::SMEM, st>>>(a, hasE);
-    return (int)cudaGetLastError();
-}
-
-template <int N>
-static int p4f(const PassArgs &a, int withE, cudaStream_t st)
-{
-    if constexpr (N <= 512) {
-        const int tiles = (a.n0 + 1) * (a.n2 / TileCfg<N>::C);
-        p4_fwd<N><<<std::min(tiles, Occ1<N>::p4), TileCfg<N>::THREADS, smem_p4<N>(), st>>>(a, withE);
-    } else {
-        using C = ColCfg<N>;
-        dim3 grid((a.n2 + C::BZ - 1) / C::BZ, a.n0 + 1);
-        p4_fwd_blk<N><<<grid, C::THREADS, C::SMEM, st>>>(a, withE);
+    const int cap_sm = sm_count();
+    if (kind == PASS_P2F) {
+        return chunked(items, n, units_tile<N>, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            const int total = w.offs[w.nitems];
+            if constexpr (N <= 512)
+                p2_fwd<N, MAXI><<<std::min(total, cap_sm * Occ1<N, MAXI>::p2), TileCfg<N>::THREADS, smem_p2<N>(), st>>>(w);
+            else
+                p2_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+            return (int)cudaGetLastError();
+        });
     }
-    return (int)cudaGetLastError();
+    if (kind == PASS_P2A) {
+        return chunked(items, n, units_blk<N>, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            p2_adj<N, MAXI><<<w.offs[w.nitems], ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w, flag);
+            return (int)cudaGetLastError();
+        });
+    }
+    if (kind == PASS_P4F) {
+        return chunked(items, n, units_tile<N>, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            const int total = w.offs[w.nitems];
+            if constexpr (N <= 512)
+                p4_fwd<N, MAXI><<<std::min(total, cap_sm * Occ1<N, MAXI>::p4), TileCfg<N>::THREADS, smem_p4<N>(), st>>>(w,
+                                                                                                                   flag);
+            else
+                p4_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w, flag);
+            return (int)cudaGetLastError();
+        });
+    }
+    return (int)cudaErrorInvalidValue;
 }
 
-int launch_p2_fwd(int N, const PassArgs &a, const float2 *src, float2 *dst, cudaStream_t st)
+int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st)
 {
     switch (N) {
-#define X(n) case n: return p2f<n>(a, src, dst, st);
-        FSP_AXIS1_SIZES(X)
-#undef X
-    default: return (int)cudaErrorInvalidValue;
-    }
-}
-
-int launch_p2_adj(int N, const PassArgs &a, int hasE, cudaStream_t st)
-{
-    switch (N) {
-#define X(n) case n: return p2a<n>(a, hasE, st);
-        FSP_AXIS1_SIZES(X)
-#undef X
-    default: return (int)cudaErrorInvalidValue;
-    }
-}
-
-int launch_p4_fwd(int N, const PassArgs &a, int withE, cudaStream_t st)
-{
-    switch (N) {
-#define X(n) case n: return p4f<n>(a, withE, st);
+#define X(v) case v: return run<v>(kind, items, n, flag, st);
         FSP_AXIS1_SIZES(X)
 #undef X
     default: return (int)cudaErrorInvalidValue;

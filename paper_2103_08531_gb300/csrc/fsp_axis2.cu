@@ -3,10 +3,56 @@
 #include "fsp_passes.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace fsp {
 
 #define FSP_AXIS2_SIZES(X) X(64) X(128) X(192) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+namespace {
+
+template <int MAXI>
+Work<MAXI> make_work(const PassArgs *items, int n, int (*units)(const PassArgs &))
+{
+    Work<MAXI> w;
+    w.nitems = n;
+    w.offs[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        w.item[i] = items[i];
+        w.offs[i + 1] = w.offs[i] + units(items[i]);
+    }
+    return w;
+}
+
+int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return sms;
+}
+
+// Launch helper: runs `body(work, grid_cap)` over items in chunks of BATCH_MAX.
+template <class F>
+int chunked(const PassArgs *items, int n, int (*units)(const PassArgs &), F body)
+{
+    if (n == 1) {
+        Work<1> w = make_work<1>(items, 1, units);
+        return body(w);
+    }
+    for (int i = 0; i < n; i += BATCH_MAX) {
+        const int m = std::min(BATCH_MAX, n - i);
+        Work<BATCH_MAX> w = make_work<BATCH_MAX>(items + i, m, units);
+        int e = body(w);
+        if (e) return e;
+    }
+    return 0;
+}
+
+} // namespace
 
 int supported_axis2(int N)
 {
@@ -18,32 +64,36 @@ int supported_axis2(int N)
     }
 }
 
-template <int N>
+template <int N, int MAXI>
 struct Occ2 {
-    static inline int p3 = 0, p3a = 0;
+    static inline int p3 = 1, p3a = 1;
 };
 
-template <int N>
-static int prep()
+template <int N, int MAXI>
+static int prep_one()
 {
     int e = 0;
     if constexpr (N <= 512) {
         using C = WarpCfg<N>;
-        e |= cudaFuncSetAttribute(p3_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        e |= cudaFuncSetAttribute(p3_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        int dev = 0, sms = 0, b = 0, ba = 0;
-        e |= cudaGetDevice(&dev);
-        e |= cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd<N>, C::THREADS, C::SMEM);
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, p3_adj<N>, C::THREADS, C::SMEM);
-        Occ2<N>::p3 = sms * (b > 0 ? b : 1);
-        Occ2<N>::p3a = sms * (ba > 0 ? ba : 1);
+        e |= cudaFuncSetAttribute(p3_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        e |= cudaFuncSetAttribute(p3_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        int b = 0, ba = 0;
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd<N, MAXI>, C::THREADS, C::SMEM);
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, p3_adj<N, MAXI>, C::THREADS, C::SMEM);
+        Occ2<N, MAXI>::p3 = std::max(1, b);
+        Occ2<N, MAXI>::p3a = std::max(1, ba);
     } else {
         using C = RowCfg<N>;
-        e |= cudaFuncSetAttribute(p3_fwd_blk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        e |= cudaFuncSetAttribute(p3_adj_blk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        e |= cudaFuncSetAttribute(p3_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        e |= cudaFuncSetAttribute(p3_adj_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     }
     return e;
+}
+
+template <int N>
+static int prep()
+{
+    return prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
 }
 
 int prepare_axis2(int N)
@@ -57,33 +107,45 @@ int prepare_axis2(int N)
 }
 
 template <int N>
-static int p3f(const PassArgs &a, int withE, cudaStream_t st)
+static int units_p3(const PassArgs &a)
 {
     const int lines = (a.n0 + 1) * a.rows1;
-    if constexpr (N <= 512) {
-        using C = WarpCfg<N>;
-        const int ctas = (lines + C::LPW * C::WARPS - 1) / (C::LPW * C::WARPS);
-        p3_fwd<N><<<std::min(ctas, Occ2<N>::p3), C::THREADS, C::SMEM, st>>>(a, withE);
-    } else {
-        using C = RowCfg<N>;
-        p3_fwd_blk<N><<<(lines + C::LPC - 1) / C::LPC, C::THREADS, C::SMEM, st>>>(a, withE);
-    }
-    return (int)cudaGetLastError();
+    if constexpr (N <= 512) return (lines + WarpCfg<N>::LPW - 1) / WarpCfg<N>::LPW;   // warp-level units
+    else return (lines + RowCfg<N>::LPC - 1) / RowCfg<N>::LPC;
 }
 
 template <int N>
-static int p3a(const PassArgs &a, int hasE, cudaStream_t st)
+static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st)
 {
-    const int lines = (a.n0 + 1) * a.rows1;
-    if constexpr (N <= 512) {
-        using C = WarpCfg<N>;
-        const int ctas = (lines + C::LPW * C::WARPS - 1) / (C::LPW * C::WARPS);
-        p3_adj<N><<<std::min(ctas, Occ2<N>::p3a), C::THREADS, C::SMEM, st>>>(a, hasE);
-    } else {
-        using C = RowCfg<N>;
-        p3_adj_blk<N><<<(lines + C::LPC - 1) / C::LPC, C::THREADS, C::SMEM, st>>>(a, hasE);
+    const int cap_sm = sm_count();
+    return chunked(items, n, units_p3<N>, [&](auto &w) {
+        constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+        const int total = w.offs[w.nitems];
+        if constexpr (N <= 512) {
+            using C = WarpCfg<N>;
+            const int ctas = (total + C::WARPS - 1) / C::WARPS;
+            if (kind == PASS_P3F)
+                p3_fwd<N, MAXI><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3), C::THREADS, C::SMEM, st>>>(w, flag);
+            else
+                p3_adj<N, MAXI><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3a), C::THREADS, C::SMEM, st>>>(w, flag);
+        } else {
+            using C = RowCfg<N>;
+            if (kind == PASS_P3F) p3_fwd_blk<N, MAXI><<<total, C::THREADS, C::SMEM, st>>>(w, flag);
+            else p3_adj_blk<N, MAXI><<<total, C::THREADS, C::SMEM, st>>>(w, flag);
+        }
+        return (int)cudaGetLastError();
+    });
+}
+
+int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st)
+{
+    if (kind != PASS_P3F && kind != PASS_P3A) return (int)cudaErrorInvalidValue;
+    switch (N) {
+#define X(v) case v: return run<v>(kind, items, n, flag, st);
+        FSP_AXIS2_SIZES(X)
+#undef X
+    default: return (int)cudaErrorInvalidValue;
     }
-    return (int)cudaGetLastError();
 }
 
 int make_twiddles_aux(float2 *tw, int N, cudaStream_t st)
@@ -94,26 +156,6 @@ int make_twiddles_aux(float2 *tw, int N, cudaStream_t st)
         X(64) X(128) X(192) X(256) X(512)
 #undef X
     default: return 0;   // block-mode lengths use the main table only
-    }
-}
-
-int launch_p3_fwd(int N, const PassArgs &a, int withE, cudaStream_t st)
-{
-    switch (N) {
-#define X(n) case n: return p3f<n>(a, withE, st);
-        FSP_AXIS2_SIZES(X)
-#undef X
-    default: return (int)cudaErrorInvalidValue;
-    }
-}
-
-int launch_p3_adj(int N, const PassArgs &a, int hasE, cudaStream_t st)
-{
-    switch (N) {
-#define X(n) case n: return p3a<n>(a, hasE, st);
-        FSP_AXIS2_SIZES(X)
-#undef X
-    default: return (int)cudaErrorInvalidValue;
     }
 }
 

@@ -40,21 +40,21 @@ int make_twiddles_aux(float2 *tw, int N, cudaStream_t st);   // fsp_axis2.cu
 constexpr int TW_AUX = 1024;   // gathered-twiddle entries after each N-entry table
 int build_kernel_spectrum(Plan *p, cudaStream_t st);
 
-// launchers (return 0 or a cudaError_t value)
+// pass kinds
+enum PassKind { PASS_P1F = 0, PASS_P1A, PASS_P2F, PASS_P2A, PASS_P3F, PASS_P3A, PASS_P4F, PASS_P5F };
+
+// launchers (return 0 or a cudaError_t value).  Each runs one pass of padded
+// length N over items[0..n) in one launch per BATCH_MAX items; flag is withE
+// (forward) or hasE (adjoint) where the pass takes one.
 int supported_axis0(int N);
 int supported_axis1(int N);
 int supported_axis2(int N);
 int prepare_axis0(int N);
 int prepare_axis1(int N);
 int prepare_axis2(int N);
-int launch_p1_fwd(int N, const PassArgs &a, float2 *dst, cudaStream_t st);
-int launch_p1_adj(int N, const PassArgs &a, cudaStream_t st);
-int launch_p5_fwd(int N, const PassArgs &a, cudaStream_t st);
-int launch_p2_fwd(int N, const PassArgs &a, const float2 *src, float2 *dst, cudaStream_t st);
-int launch_p2_adj(int N, const PassArgs &a, int hasE, cudaStream_t st);
-int launch_p4_fwd(int N, const PassArgs &a, int withE, cudaStream_t st);
-int launch_p3_fwd(int N, const PassArgs &a, int withE, cudaStream_t st);
-int launch_p3_adj(int N, const PassArgs &a, int hasE, cudaStream_t st);
+int launch_axis0(int kind, int N, const PassArgs *items, int n, cudaStream_t st);
+int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st);
+int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st);
 
 } // namespace fsp
 

@@ -57,6 +57,39 @@ __device__ __forceinline__ float wave(int k, int n, float s)
     return s * (float)m;
 }
 
+// A launch's work: up to MAXI independent problems (items), item i owning
+// work units [offs[i], offs[i+1]).  Passed by value as a __grid_constant__
+// kernel parameter, so a batch of solves needs no device-side scratch.
+template <int MAXI>
+struct Work {
+    static constexpr int max_items = MAXI;
+    PassArgs item[MAXI];
+    int offs[MAXI + 1];
+    int nitems;
+    __device__ __forceinline__ int count() const { return offs[nitems]; }
+    // item owning unit w: the last i with offs[i] <= w
+    __device__ __forceinline__ int find(int w) const
+    {
+        if constexpr (MAXI == 1) {
+            return 0;
+        } else {
+            int lo = 0, hi = nitems - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (offs[mid] <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            return lo;
+        }
+    }
+};
+constexpr int BATCH_MAX = 32;   // items per batched launch
+
+#define FSP_UNIT(W, w, a, u)                  \
+    const int it_##u = (W).find(w);           \
+    const PassArgs &a = (W).item[it_##u];     \
+    const int u = (w) - (W).offs[it_##u]
+
 template <int N>
 struct ColCfg {
     static constexpr int E = Plan1D<N>::E;
@@ -72,7 +105,7 @@ struct RowCfg {
     static constexpr int T = N / E;
     static constexpr int LPC = (T >= 256) ? 1 : (256 / T);
     static constexpr int THREADS = T * LPC;
-    static constexpr int PAD = 3;
+    static constexpr int PAD = 4;
     static constexpr int SPAN = RowSpan<N, PAD>::value;
     static constexpr size_t SMEM = (size_t)SPAN * LPC * sizeof(float2);
 };
@@ -80,18 +113,21 @@ struct RowCfg {
 // ----------------------------------------------------------------- P1 (axis 0)
 
 // Forward: rho columns (z, z+1) packed as re/im; output rows 0..n1-1 of buf_out.
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_blk(PassArgs a, float2 *__restrict__ dst)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_blk(const __grid_constant__ Work<MAXI> W)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    const int y = blockIdx.y;
-    const int z0 = 2 * (blockIdx.x * BZ + col);
+    FSP_UNIT(W, blockIdx.x, a, u);
+    const int xt = (a.n2 / 2 + BZ - 1) / BZ;
+    const int y = u / xt;
+    const int z0 = 2 * ((u % xt) * BZ + col);
     const bool act = z0 < a.n2;
     const float *rho = a.in[0];
+    float2 *__restrict__ dst = a.three_d ? a.buf1 : a.buf0;
     float2 v[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -123,16 +159,18 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_blk(PassArgs a, flo
 // Adjoint: per column z, W1 = g_phi + i g_E0, W2 = g_E1 + i g_E2 (3D) or g_E1 (2D).
 // Outputs U = F g_phi + i k0 F g_E0 -> buf0 row y; F g_E1 -> buf0 row n1 + y (3D)
 // or buf1 row y (2D); F g_E2 -> buf1 row y (3D).
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_adj(PassArgs a)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_adj(const __grid_constant__ Work<MAXI> W)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    const int y = blockIdx.y;
-    const int z = blockIdx.x * BZ + col;
+    FSP_UNIT(W, blockIdx.x, a, u);
+    const int xt = (a.n2 + BZ - 1) / BZ;
+    const int y = u / xt;
+    const int z = (u % xt) * BZ + col;
     const bool act = z < a.n2;
     const float *gp = a.in[0], *g0 = a.in[1], *g1 = a.in[2], *g2 = a.in[3];
     const bool hasE = g0 != nullptr;
@@ -182,17 +220,21 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_adj(PassArgs a)
 // ----------------------------------------------------------------- P2 (axis 1)
 
 // Forward: src rows 0..n1-1 -> dst rows 0..2n1-1.
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd_blk(PassArgs a, const float2 *__restrict__ src, float2 *__restrict__ dst)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd_blk(const __grid_constant__ Work<MAXI> W)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    const int kx = blockIdx.y;
-    const int z = blockIdx.x * BZ + col;
+    FSP_UNIT(W, blockIdx.x, a, u);
+    const int xt = (a.n2 + BZ - 1) / BZ;
+    const int kx = u / xt;
+    const int z = (u % xt) * BZ + col;
     const bool act = z < a.n2;
+    const float2 *__restrict__ src = a.buf1;
+    float2 *__restrict__ dst = a.buf0;
     float2 v[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -208,16 +250,18 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd_blk(PassArgs a, con
 
 // Adjoint: buf0 rows [0,n1) = U, rows [n1,2n1) = F g_E1 (if E), buf1 rows [0,n1) = F g_E2.
 // buf0 <- F1 U + i k1 F1 (F g_E1) (all rows); buf1 <- F1 (F g_E2) (all rows).
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_adj(PassArgs a, int hasE)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_adj(const __grid_constant__ Work<MAXI> W, int hasE)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    const int kx = blockIdx.y;
-    const int z = blockIdx.x * BZ + col;
+    FSP_UNIT(W, blockIdx.x, a, u);
+    const int xt = (a.n2 + BZ - 1) / BZ;
+    const int kx = u / xt;
+    const int z = (u % xt) * BZ + col;
     const bool act = z < a.n2;
     const int n1 = a.n1;
     ColView sm{smem + col, BZ};
@@ -272,16 +316,17 @@ __device__ __forceinline__ const float *krow(const PassArgs &a, int kx, int row)
 
 // Forward: line of buf0 -> F2 -> x K -> inverse -> buf0 (phi stream), and
 // -i k2 K -> inverse -> buf1 (E2 stream) when withE.
-template <int N>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(PassArgs a, int withE)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_constant__ Work<MAXI> W, int withE)
 {
     using C = RowCfg<N>;
     constexpr int E = C::E, T = C::T, LPC = C::LPC;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int li = threadIdx.x / T, j = threadIdx.x % T;
+    FSP_UNIT(W, blockIdx.x, a, u);
     const int lines = (a.n0 + 1) * a.rows1;
-    const int line = blockIdx.x * LPC + li;
+    const int line = u * LPC + li;
     const bool act = line < lines;
     const int lc = act ? line : 0;
     const int kx = lc / a.rows1, row = lc % a.rows1;
@@ -297,7 +342,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(PassArgs a, int
     }
     line_fft<N, E, false, true, RAD>(v, j, a.tw2, sm);
     const float *Kr = krow(a, kx, row);
-    float2 u[E];
+    float2 q[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int k = j + r * T;
@@ -305,7 +350,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(PassArgs a, int
         const float kv = act ? __ldg(Kr + kf) : 0.f;
         v[r] = kv * v[r];
         const float kk = wave(k, n2, a.k2s);
-        u[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
+        q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
     }
     line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
     if (act) {
@@ -313,25 +358,26 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(PassArgs a, int
         for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
     }
     if (withE) {
-        line_fft<N, E, true, false, RAD>(u, j, a.tw2, sm);
+        line_fft<N, E, true, false, RAD>(q, j, a.tw2, sm);
         if (act) {
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
+            for (int r = 0; r < E / 2; ++r) L1[j + r * T] = q[r];
         }
     }
 }
 
 // Adjoint: buf0 line V (and buf1 line Z when hasE) -> K (F2 V + i k2 F2 Z) -> inverse -> buf0.
-template <int N>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj_blk(PassArgs a, int hasE)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj_blk(const __grid_constant__ Work<MAXI> W, int hasE)
 {
     using C = RowCfg<N>;
     constexpr int E = C::E, T = C::T, LPC = C::LPC;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int li = threadIdx.x / T, j = threadIdx.x % T;
+    FSP_UNIT(W, blockIdx.x, a, u);
     const int lines = (a.n0 + 1) * a.rows1;
-    const int line = blockIdx.x * LPC + li;
+    const int line = u * LPC + li;
     const bool act = line < lines;
     const int lc = act ? line : 0;
     const int kx = lc / a.rows1, row = lc % a.rows1;
@@ -378,26 +424,28 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_adj_blk(PassArgs a, int
 
 // Forward: buf0 (phi stream, all rows) -> inverse -> rows [0,n1); with E also
 // -i k1 phi -> rows [n1,2n1) of buf0 and buf1 (E2 stream) -> rows [0,n1) of buf1.
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd_blk(PassArgs a, int withE)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd_blk(const __grid_constant__ Work<MAXI> W, int withE)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    const int kx = blockIdx.y;
-    const int z = blockIdx.x * BZ + col;
+    FSP_UNIT(W, blockIdx.x, a, u);
+    const int xt = (a.n2 + BZ - 1) / BZ;
+    const int kx = u / xt;
+    const int z = (u % xt) * BZ + col;
     const bool act = z < a.n2;
     const int zc = act ? z : 0;
     const int n1 = a.n1;
     ColView sm{smem + col, BZ};
-    float2 v[E], u[E];
+    float2 v[E], q[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         v[r] = a.buf0[iidx(a, kx, j + r * T, zc)];
         const float kk = wave(j + r * T, n1, a.k1s);
-        u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+        q[r] = make_float2(kk * v[r].y, -kk * v[r].x);
     }
     line_fft<N, E, true, false, RAD>(v, j, a.tw1, sm);
     if (act) {
@@ -405,10 +453,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd_blk(PassArgs a, int
         for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
     }
     if (withE) {
-        line_fft<N, E, true, false, RAD>(u, j, a.tw1, sm);
+        line_fft<N, E, true, false, RAD>(q, j, a.tw1, sm);
         if (act) {
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = u[r];
+            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = q[r];
         }
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = a.buf1[iidx(a, kx, j + r * T, zc)];
@@ -425,16 +473,18 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd_blk(PassArgs a, int
 // Forward: phi stream (buf0 rows [0,n1)) -> (phi, E0) via W = (1 + k0) P; E1/E2
 // streams -> (E1, E2) via W = Y + i Z (3D: Y = buf0 rows n1 + y, Z = buf1 rows
 // y; 2D: Y = buf1 row 0, Z absent).  Adjoint uses mode phi-only.
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(PassArgs a)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_constant__ Work<MAXI> W)
 {
     using C = ColCfg<N>;
     constexpr int E = C::E, T = C::T, BZ = C::BZ;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    const int y = blockIdx.y;
-    const int z = blockIdx.x * BZ + col;
+    FSP_UNIT(W, blockIdx.x, a, u);
+    const int xt = (a.n2 + BZ - 1) / BZ;
+    const int y = u / xt;
+    const int z = (u % xt) * BZ + col;
     const bool act = z < a.n2;
     const int zc = act ? z : 0;
     constexpr int NH = N / 2;
@@ -546,9 +596,10 @@ __device__ __forceinline__ void issue_rows(float2 *dst, const void *src, size_t 
     }
 }
 
-// P1: rho pairs (z, z+1) -> half spectrum in k0, output rows 0..n1-1 of dst.
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(PassArgs a, float2 *__restrict__ dst)
+// P1: rho pairs (z, z+1) -> half spectrum in k0, output rows 0..n1-1 of buf1
+// (3D) or buf0 (2D).  Unit: (y, tile of 2C reals of axis 2).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(const __grid_constant__ Work<MAXI> W)
 {
     using C = TileCfg<N>;
     constexpr int CC = C::C;
@@ -557,25 +608,29 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(PassArgs a, float2
     extern __shared__ float2 smem[];
     float2 *stage = smem, *ex = smem + NH * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
-    const int zt = a.n2 / (2 * CC), ntiles = a.n1 * zt;
-    const size_t rstride = (size_t)a.n1 * a.n2 * sizeof(float);
-    auto issue = [&](int t) {
-        const int y = t / zt, z0 = (t % zt) * (2 * CC);
-        issue_rows<CC>(stage, a.in[0] + gidx(a, 0, y, z0), rstride, NH, tid, C::THREADS);
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / (2 * CC);
+        const int y = u / zt, z0 = (u % zt) * (2 * CC);
+        issue_rows<CC>(stage, a.in[0] + gidx(a, 0, y, z0), (size_t)a.n1 * a.n2 * sizeof(float), NH, tid, C::THREADS);
     };
-    int t = blockIdx.x;
-    if (t < ntiles) issue(t);
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
-    for (; t < ntiles; t += gridDim.x) {
+    for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int y = t / zt, z0 = (t % zt) * (2 * CC) + 2 * col;
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / (2 * CC);
+        const int y = u / zt, z0 = (u % zt) * (2 * CC) + 2 * col;
+        float2 *__restrict__ dst = a.three_d ? a.buf1 : a.buf0;
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
         __syncthreads();
-        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
         line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
 #pragma unroll
@@ -585,13 +640,13 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(PassArgs a, float2
         for (int r = 0; r <= E / 2; ++r) {
             const int k = j + r * T;
             if (k <= NH) {
-                const float2 w = v[r];
+                const float2 q = v[r];
                 const float2 m = sm.at(k == 0 ? 0 : N - k);
                 float4 o;
-                o.x = 0.5f * (w.x + m.x);
-                o.y = 0.5f * (w.y - m.y);
-                o.z = 0.5f * (w.y + m.y);
-                o.w = -0.5f * (w.x - m.x);
+                o.x = 0.5f * (q.x + m.x);
+                o.y = 0.5f * (q.y - m.y);
+                o.z = 0.5f * (q.y + m.y);
+                o.w = -0.5f * (q.x - m.x);
                 *reinterpret_cast<float4 *>(dst + iidx(a, k, y, z0)) = o;
             }
         }
@@ -599,10 +654,9 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(PassArgs a, float2
     cp_async_wait_all();
 }
 
-// P2: buf_src rows 0..n1-1 -> forward axis 1 -> dst rows 0..2n1-1.
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(PassArgs a, const float2 *__restrict__ src,
-                                                              float2 *__restrict__ dst)
+// P2: buf1 rows 0..n1-1 -> forward axis 1 -> buf0 rows 0..2n1-1.  Unit: (k0, tile of C columns).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(const __grid_constant__ Work<MAXI> W)
 {
     using C = TileCfg<N>;
     constexpr int CC = C::C;
@@ -611,37 +665,40 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(PassArgs a, const 
     extern __shared__ float2 smem[];
     float2 *stage = smem, *ex = smem + NH * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
-    const int zt = a.n2 / CC, ntiles = (a.n0 + 1) * zt;
-    const size_t rstride = (size_t)a.n2 * sizeof(float2);
-    auto issue = [&](int t) {
-        const int kx = t / zt, z0 = (t % zt) * CC;
-        issue_rows<CC>(stage, src + iidx(a, kx, 0, z0), rstride, NH, tid, C::THREADS);
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int kx = u / zt, z0 = (u % zt) * CC;
+        issue_rows<CC>(stage, a.buf1 + iidx(a, kx, 0, z0), (size_t)a.n2 * sizeof(float2), NH, tid, C::THREADS);
     };
-    int t = blockIdx.x;
-    if (t < ntiles) issue(t);
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
-    for (; t < ntiles; t += gridDim.x) {
+    for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int kx = t / zt, z = (t % zt) * CC + col;
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int kx = u / zt, z = (u % zt) * CC + col;
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
         __syncthreads();
-        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
         line_fft<N, E, false, true, RAD>(v, j, a.tw1, sm);
 #pragma unroll
-        for (int r = 0; r < E; ++r) dst[iidx(a, kx, j + r * T, z)] = v[r];
+        for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
     }
     cp_async_wait_all();
 }
 
 // P4: buf0 (phi stream, 2 n1 rows) -> rows [0,n1) phi, rows [n1,2n1) -i k1 phi;
-// buf1 (E2 stream) -> rows [0,n1).
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(PassArgs a, int withE)
+// buf1 (E2 stream) -> rows [0,n1).  Unit: (k0, tile of C columns).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(const __grid_constant__ Work<MAXI> W, int withE)
 {
     using C = TileCfg<N>;
     constexpr int CC = C::C;
@@ -650,42 +707,47 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(PassArgs a, int wi
     extern __shared__ float2 smem[];
     float2 *st0 = smem, *st1 = smem + N * CC, *ex = smem + 2 * N * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
-    const int n1 = a.n1, zt = a.n2 / CC, ntiles = (a.n0 + 1) * zt;
-    const size_t rstride = (size_t)a.n2 * sizeof(float2);
-    auto issue = [&](int t) {
-        const int kx = t / zt, z0 = (t % zt) * CC;
-        issue_rows<CC>(st0, a.buf0 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
-        if (withE) issue_rows<CC>(st1, a.buf1 + iidx(a, kx, 0, z0), rstride, N, tid, C::THREADS);
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int kx = u / zt, z0 = (u % zt) * CC;
+        const size_t rs = (size_t)a.n2 * sizeof(float2);
+        issue_rows<CC>(st0, a.buf0 + iidx(a, kx, 0, z0), rs, N, tid, C::THREADS);
+        if (withE) issue_rows<CC>(st1, a.buf1 + iidx(a, kx, 0, z0), rs, N, tid, C::THREADS);
     };
-    int t = blockIdx.x;
-    if (t < ntiles) issue(t);
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
-    for (; t < ntiles; t += gridDim.x) {
+    for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int kx = t / zt, z = (t % zt) * CC + col;
-        float2 v[E], w[E];
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int kx = u / zt, z = (u % zt) * CC + col;
+        const int n1 = a.n1;
+        float2 v[E], q[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             v[r] = st0[(j + r * T) * CC + col];
-            w[r] = withE ? st1[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
+            q[r] = withE ? st1[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
         if (withE) {
-            line_fft<N, E, true, false, RAD>(w, j, a.tw1, sm);
+            line_fft<N, E, true, false, RAD>(q, j, a.tw1, sm);
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = w[r];
+            for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = q[r];
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const float kk = wave(j + r * T, n1, a.k1s);
-                w[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+                q[r] = make_float2(kk * v[r].y, -kk * v[r].x);
             }
-            line_fft<N, E, true, false, RAD>(w, j, a.tw1, sm);
+            line_fft<N, E, true, false, RAD>(q, j, a.tw1, sm);
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = w[r];
+            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = q[r];
         }
         line_fft<N, E, true, false, RAD>(v, j, a.tw1, sm);
 #pragma unroll
@@ -694,9 +756,9 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(PassArgs a, int wi
     cp_async_wait_all();
 }
 
-// P5: half spectra in k0 -> real outputs (see the header comment).
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
+// P5: half spectra in k0 -> real outputs (see the header comment).  Unit: (y, tile of C columns).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(const __grid_constant__ Work<MAXI> W)
 {
     using C = TileCfg<N>;
     constexpr int CC = C::C;
@@ -704,32 +766,36 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
     float2 *sA = smem, *sB = smem + ROWS * CC, *sC = smem + 2 * ROWS * CC, *ex = smem + 3 * ROWS * CC;
-    float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
-    const bool first = phi || e0, second = e1 != nullptr;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
-    const int zt = a.n2 / CC, ntiles = a.n1 * zt;
-    const size_t rstride = (size_t)a.rows1 * a.n2 * sizeof(float2);
-    auto issue = [&](int t) {
-        const int y = t / zt, z0 = (t % zt) * CC;
-        if (first) issue_rows<CC>(sA, a.buf0 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
-        if (second) {
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int y = u / zt, z0 = (u % zt) * CC;
+        const size_t rs = (size_t)a.rows1 * a.n2 * sizeof(float2);
+        if (a.out[0] || a.out[1]) issue_rows<CC>(sA, a.buf0 + iidx(a, 0, y, z0), rs, ROWS, tid, C::THREADS);
+        if (a.out[2]) {
             if (a.three_d) {
-                issue_rows<CC>(sB, a.buf0 + iidx(a, 0, a.n1 + y, z0), rstride, ROWS, tid, C::THREADS);
-                issue_rows<CC>(sC, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+                issue_rows<CC>(sB, a.buf0 + iidx(a, 0, a.n1 + y, z0), rs, ROWS, tid, C::THREADS);
+                issue_rows<CC>(sC, a.buf1 + iidx(a, 0, y, z0), rs, ROWS, tid, C::THREADS);
             } else {
-                issue_rows<CC>(sB, a.buf1 + iidx(a, 0, y, z0), rstride, ROWS, tid, C::THREADS);
+                issue_rows<CC>(sB, a.buf1 + iidx(a, 0, y, z0), rs, ROWS, tid, C::THREADS);
             }
         }
     };
-    int t = blockIdx.x;
-    if (t < ntiles) issue(t);
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
-    for (; t < ntiles; t += gridDim.x) {
+    for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
-        const int y = t / zt, z = (t % zt) * CC + col;
-        float2 v[E], w[E];
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int y = u / zt, z = (u % zt) * CC + col;
+        float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
+        const bool first = phi || e0, second = e1 != nullptr;
+        float2 v[E], q[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int k = j + r * T;
@@ -747,10 +813,10 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
             }
             if (e0) p = (1.f + wave(k, NH, a.k0s)) * p;   // W = P + i (-i k0 P)
             v[r] = p;
-            w[r] = make_float2(Y.x - Z.y, Y.y + Z.x);        // Y + i Z
+            q[r] = make_float2(Y.x - Z.y, Y.y + Z.x);        // Y + i Z
         }
         __syncthreads();
-        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
         if (first) {
             line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
@@ -762,12 +828,12 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(PassArgs a)
             }
         }
         if (second) {
-            line_fft<N, E, true, false, RAD>(w, j, a.tw0, sm);
+            line_fft<N, E, true, false, RAD>(q, j, a.tw0, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) {
                 const size_t g = gidx(a, j + r * T, y, z);
-                e1[g] = w[r].x;
-                if (a.three_d) e2[g] = w[r].y;
+                e1[g] = q[r].x;
+                if (a.three_d) e2[g] = q[r].y;
             }
         }
     }
@@ -810,9 +876,11 @@ struct WarpCfg {
 };
 
 // Forward middle pass, one warp per line (or per 32/T lines), persistent over
-// lines with the next line's input prefetched into registers.
-template <int N>
-__global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(PassArgs a, int withE)
+// lines with the next line's input prefetched into registers.  Unit: a group
+// of LPW lines of one item (warp-level).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(const __grid_constant__ Work<MAXI> W,
+                                                                           int withE)
 {
     using C = WarpCfg<N>;
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
@@ -820,105 +888,70 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(PassA
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
-    const int n2 = a.n2;
-    const int lines = (a.n0 + 1) * a.rows1;
-    const int groups = (lines + LPW - 1) / LPW;
+    const int nw = W.count();
     const int gstride = gridDim.x * C::WARPS;
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
     int g = blockIdx.x * C::WARPS + warp;
     float2 pv[E / 2];
-    if (FSP_P3_PREFETCH) {
-        const int line = g * LPW + li;
-        const bool act = g < groups && line < lines;
-        const float2 *L = a.buf0 + (size_t)(act ? line : 0) * n2;
 #pragma unroll
-        for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
-    }
-    for (; g < groups; g += gstride) {
-        const int line = g * LPW + li;
-        const bool act = line < lines;
-        const int lc = act ? line : 0;
-        float2 v[E];
-        if (!FSP_P3_PREFETCH) {
-            const float2 *L = a.buf0 + (size_t)lc * n2;
+    for (int r = 0; r < E / 2; ++r) pv[r] = make_float2(0.f, 0.f);
+    // loads line group gg into pv (left unchanged when gg is past the end)
+    auto fetch = [&](int gg) {
+        if (gg < nw) {
+            FSP_UNIT(W, gg, b, ub);
+            const int bline = ub * LPW + li;
+            if (bline < (b.n0 + 1) * b.rows1) {
+                const float2 *L = b.buf0 + (size_t)bline * b.n2;
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
+                for (int r = 0; r < E / 2; ++r) pv[r] = L[j + r * T];
+            }
         }
+    };
+    if (FSP_P3_PREFETCH) fetch(g);
+    for (; g < nw; g += gstride) {
+        if (!FSP_P3_PREFETCH) fetch(g);
+        float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
-        if (FSP_P3_PREFETCH) {
-            const int ng = g + gstride;
-            const int nline = ng * LPW + li;
-            const bool nact = ng < groups && nline < lines;
-            const float2 *L = a.buf0 + (size_t)(nact ? nline : 0) * n2;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r)
-                if (nact) pv[r] = L[j + r * T];
-        }
+        if (FSP_P3_PREFETCH) fetch(g + gstride);
+        FSP_UNIT(W, g, a, u);
+        const int n2 = a.n2;
+        const int lines = (a.n0 + 1) * a.rows1;
+        const int line = u * LPW + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
         const int kx = lc / a.rows1, row = lc % a.rows1;
         line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
         const float *Kr = krow(a, kx, row);
-        if constexpr (C::SAVE) {
-            float2 *sv = smem + C::SPAN * LPW * C::WARPS + (size_t)(warp * LPW + li) * N;
+        float2 q[E];
 #pragma unroll
-            for (int r = 0; r < E; ++r) {
-                const int k = j + r * T;
-                const int kf = k <= n2 ? k : N - k;
-                v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
-                if (withE) sv[k] = v[r];
-            }
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int kf = k <= n2 ? k : N - k;
+            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+            const float kk = wave(k, n2, a.k2s);
+            q[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+        }
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        if (act) {
+            float2 *L0 = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+        }
+        if (withE) {
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(q, j, a.tw2, sm);
             if (act) {
-                float2 *L0 = a.buf0 + (size_t)lc * n2;
+                float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
-                for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
-            }
-            if (withE) {
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
-                    const int k = j + r * T;
-                    const float kk = wave(k, n2, a.k2s);
-                    const float2 sk = sv[k];
-                    v[r] = make_float2(kk * sk.y, -kk * sk.x);
-                }
-                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
-                if (act) {
-                    float2 *L1 = a.buf1 + (size_t)lc * n2;
-#pragma unroll
-                    for (int r = 0; r < E / 2; ++r) L1[j + r * T] = v[r];
-                }
-            }
-        } else {
-            float2 u[E];
-#pragma unroll
-            for (int r = 0; r < E; ++r) {
-                const int k = j + r * T;
-                const int kf = k <= n2 ? k : N - k;
-                v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
-                const float kk = wave(k, n2, a.k2s);
-                u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
-            }
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
-            if (act) {
-                float2 *L0 = a.buf0 + (size_t)lc * n2;
-#pragma unroll
-                for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
-            }
-            if (withE) {
-                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, a.tw2, sm);
-                if (act) {
-                    float2 *L1 = a.buf1 + (size_t)lc * n2;
-#pragma unroll
-                    for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
-                }
+                for (int r = 0; r < E / 2; ++r) L1[j + r * T] = q[r];
             }
         }
     }
 }
 
-// Adjoint middle pass, warp per line.
-template <int N>
-__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(PassArgs a, int hasE)
+// Adjoint middle pass, warp per line group.
+template <int N, int MAXI>
+__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_constant__ Work<MAXI> W, int hasE)
 {
     using C = WarpCfg<N>;
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
@@ -926,12 +959,13 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(PassArgs a, int ha
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
-    const int n2 = a.n2;
-    const int lines = (a.n0 + 1) * a.rows1;
-    const int groups = (lines + LPW - 1) / LPW;
+    const int nw = W.count();
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
-    for (int g = blockIdx.x * C::WARPS + warp; g < groups; g += gridDim.x * C::WARPS) {
-        const int line = g * LPW + li;
+    for (int g = blockIdx.x * C::WARPS + warp; g < nw; g += gridDim.x * C::WARPS) {
+        FSP_UNIT(W, g, a, u);
+        const int n2 = a.n2;
+        const int lines = (a.n0 + 1) * a.rows1;
+        const int line = u * LPW + li;
         const bool act = line < lines;
         const int lc = act ? line : 0;
         float2 *L0 = a.buf0 + (size_t)lc * n2;
@@ -941,14 +975,14 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(PassArgs a, int ha
         for (int r = 0; r < E; ++r) v[r] = (r < E / 2 && act) ? L0[j + r * T] : make_float2(0.f, 0.f);
         line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
         if (hasE) {
-            float2 w[E];
+            float2 q[E];
 #pragma unroll
-            for (int r = 0; r < E; ++r) w[r] = (r < E / 2 && act) ? L1[j + r * T] : make_float2(0.f, 0.f);
-            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(w, j, a.tw2, sm);
+            for (int r = 0; r < E; ++r) q[r] = (r < E / 2 && act) ? L1[j + r * T] : make_float2(0.f, 0.f);
+            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(q, j, a.tw2, sm);
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const float kk = wave(j + r * T, n2, a.k2s);
-                v[r] = make_float2(v[r].x - kk * w[r].y, v[r].y + kk * w[r].x);
+                v[r] = make_float2(v[r].x - kk * q[r].y, v[r].y + kk * q[r].x);
             }
         }
         const int kx = lc / a.rows1, row = lc % a.rows1;

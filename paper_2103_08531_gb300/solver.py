@@ -179,6 +179,20 @@ class Batch:
         _lib.check(self.lib.fsp_batch_solve(self.handle, _stream(stream)), "fsp_batch_solve")
         return self.phis, self.Es
 
+    def capture(self, warmup: int = 1):
+        """Record run() into a torch.cuda.CUDAGraph; replay with graph.replay()."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.fsp_batch_destroy(self.handle)

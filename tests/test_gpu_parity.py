@@ -230,6 +230,38 @@ def test_batched_equals_single(fsp):
         assert torch.equal(bph, ph1) and torch.equal(bE, E1)
 
 
+def test_batched_many_mixed_items_and_graph(fsp):
+    """More items than one launch holds (chunks), 2D and 3D mixed, uneven shapes; graph replay."""
+    rng = np.random.default_rng(44)
+    specs = []
+    shapes3 = [(32, 32, 32), (64, 32, 32), (32, 64, 96), (96, 32, 64), (32, 32, 128), (64, 64, 64)]
+    for i in range(40):
+        if i % 5 == 4:
+            s = (64, 128) if i % 2 else (128, 64)
+        else:
+            s = shapes3[i % len(shapes3)]
+        h = tuple(float(x) for x in rng.uniform(0.01, 0.03, size=len(s)))
+        specs.append((s, h))
+    plans = [fsp.Plan(s, h, "vgf") for s, h in specs]
+    rhos = [torch.from_numpy(_mixture(s, h, 100 + i, count=1).rho(np.float32)).cuda() for i, (s, h) in enumerate(specs)]
+    batch = fsp.Batch(plans, rhos)
+    g = batch.capture()
+    for r in rhos:
+        r.mul_(2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    for p, r, ph, E in zip(plans, rhos, batch.phis, batch.Es):
+        ph1, E1 = p.solve(r)
+        assert torch.equal(ph, ph1) and torch.equal(E, E1)
+
+
+def test_batched_rejects_repeated_plan(fsp):
+    p = fsp.Plan((32, 32, 32), (0.02, 0.02, 0.02), "vgf")
+    r = torch.zeros((32, 32, 32), device="cuda")
+    with pytest.raises(fsp.FspError):
+        fsp.solve_batched([p, p], [r, r])
+
+
 # ------------------------------------------------------------ full sizes
 
 def test_full_size_256_vgf_against_oracle(fsp, oracle_mod):
