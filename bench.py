@@ -429,17 +429,29 @@ def run_other(args):
         rho = torch.from_numpy(prob.rho(np.float32)).cuda()
         res = {}
         clocks.start()
+        per_pass = None
         for m in ("vgf", "he"):
             plan = fsp.Plan(prob.shape, prob.h, m)
             phi = torch.empty_like(rho)
             E = torch.empty((2,) + prob.shape, device="cuda")
             res[m] = _timed(lambda: plan.solve(rho, phi=phi, E=E), args.steps, args.warmup) / args.steps
+            if m == "vgf":
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                for e in evs:
+                    e.record()
+                plan.set_pass_events(evs)
+                plan.solve(rho, phi=phi, E=E)
+                torch.cuda.synchronize()
+                plan.set_pass_events(None)
+                per_pass = dict(zip(["p1_fwd", "p3_fwd", "p5_fwd"], [evs[i].elapsed_time(evs[i + 1]) for i in range(3)]))
         clk = clocks.stop()
         byts = sum(pass_bytes_2d(prob.shape).values())
         per = res["vgf"]
         line.update({"metric": "2D VGF solves/s at 4096^2 FP32 (phi+E)", "value": 1e3 / per, "unit": "solves/s",
                      "ms_per_step": per, "config": {"workload": "2D VGF 4096^2 on [-1,1]^2, 16 Gaussians (seed 2)"},
                      "gpts_per_s": prob.points / (per * 1e-3) / 1e9, "he_ms_per_step": res["he"],
+                     "per_pass_ms": per_pass,
+                     "per_pass_gbs": {k: pass_bytes_2d(prob.shape)[k] / (t * 1e-3) / 1e9 for k, t in per_pass.items()},
                      "pipeline": {"bytes": byts, "gbs": byts / (per * 1e-3) / 1e9,
                                   "frac": byts / (per * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
                      "gpu_launches": 3 * args.steps, "clocks": clk})

@@ -66,7 +66,7 @@ int supported_axis2(int N)
 
 template <int N, int MAXI>
 struct Occ2 {
-    static inline int p3 = 1, p3a = 1;
+    static inline int p3 = 1, p3a = 1, p3one = 1;
 };
 
 template <int N, int MAXI>
@@ -76,6 +76,12 @@ static int prep_one()
     if constexpr (N <= 512) {
         using C = WarpCfg<N>;
         e |= cudaFuncSetAttribute(p3_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if constexpr (MAXI == 1) {
+            e |= cudaFuncSetAttribute(p3_fwd1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            int b1 = 0;
+            e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p3_fwd1<N>, C::THREADS, C::SMEM);
+            Occ2<N, MAXI>::p3one = std::max(1, b1);
+        }
         e |= cudaFuncSetAttribute(p3_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         int b = 0, ba = 0;
         e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd<N, MAXI>, C::THREADS, C::SMEM);
@@ -124,7 +130,9 @@ static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st
         if constexpr (N <= 512) {
             using C = WarpCfg<N>;
             const int ctas = (total + C::WARPS - 1) / C::WARPS;
-            if (kind == PASS_P3F)
+            if (kind == PASS_P3F && MAXI == 1)
+                p3_fwd1<N><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3one), C::THREADS, C::SMEM, st>>>(w.item[0], flag);
+            else if (kind == PASS_P3F)
                 p3_fwd<N, MAXI><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3), C::THREADS, C::SMEM, st>>>(w, flag);
             else
                 p3_adj<N, MAXI><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3a), C::THREADS, C::SMEM, st>>>(w, flag);

@@ -855,8 +855,12 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(const __grid_const
 #ifndef FSP_P3_PREFETCH
 #define FSP_P3_PREFETCH 1
 #endif
-#ifndef FSP_P3_MINB
-#define FSP_P3_MINB 1
+// Optional minimum resident blocks for the middle pass.  Leave unset: a
+// bound of 1 lets the compiler take far more registers (measured slower).
+#ifdef FSP_P3_MINB
+#define FSP_P3_BOUNDS(t) __launch_bounds__(t, FSP_P3_MINB)
+#else
+#define FSP_P3_BOUNDS(t) __launch_bounds__(t)
 #endif
 template <int N>
 using P3Plan = typename std::conditional<FSP_P3_E32 != 0, Plan32<N>, Plan16<N>>::type;
@@ -879,7 +883,7 @@ struct WarpCfg {
 // lines with the next line's input prefetched into registers.  Unit: a group
 // of LPW lines of one item (warp-level).
 template <int N, int MAXI>
-__global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(const __grid_constant__ Work<MAXI> W,
+__global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant__ Work<MAXI> W,
                                                                            int withE)
 {
     using C = WarpCfg<N>;
@@ -888,38 +892,48 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(const
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
-    const int nw = W.count();
+    // (the single-item bound is computed from the geometry: the register
+    // allocation of this kernel is sensitive to where the bound comes from)
+    const int nw = MAXI == 1 ? ((W.item[0].n0 + 1) * W.item[0].rows1 + LPW - 1) / LPW : W.count();
     const int gstride = gridDim.x * C::WARPS;
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
     int g = blockIdx.x * C::WARPS + warp;
     float2 pv[E / 2];
+    if (FSP_P3_PREFETCH) {
+        const int it = W.find(g < nw ? g : 0);
+        const PassArgs &b = W.item[it];
+        const int bline = (g - W.offs[it]) * LPW + li;
+        const bool bact = g < nw && bline < (b.n0 + 1) * b.rows1;
+        const float2 *L = b.buf0 + (size_t)(bact ? bline : 0) * b.n2;
 #pragma unroll
-    for (int r = 0; r < E / 2; ++r) pv[r] = make_float2(0.f, 0.f);
-    // loads line group gg into pv (left unchanged when gg is past the end)
-    auto fetch = [&](int gg) {
-        if (gg < nw) {
-            FSP_UNIT(W, gg, b, ub);
-            const int bline = ub * LPW + li;
-            if (bline < (b.n0 + 1) * b.rows1) {
-                const float2 *L = b.buf0 + (size_t)bline * b.n2;
-#pragma unroll
-                for (int r = 0; r < E / 2; ++r) pv[r] = L[j + r * T];
-            }
-        }
-    };
-    if (FSP_P3_PREFETCH) fetch(g);
+        for (int r = 0; r < E / 2; ++r) pv[r] = bact ? L[j + r * T] : make_float2(0.f, 0.f);
+    }
     for (; g < nw; g += gstride) {
-        if (!FSP_P3_PREFETCH) fetch(g);
-        float2 v[E];
-#pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
-        if (FSP_P3_PREFETCH) fetch(g + gstride);
         FSP_UNIT(W, g, a, u);
         const int n2 = a.n2;
         const int lines = (a.n0 + 1) * a.rows1;
         const int line = u * LPW + li;
         const bool act = line < lines;
         const int lc = act ? line : 0;
+        float2 v[E];
+        if (!FSP_P3_PREFETCH) {
+            const float2 *L = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
+        if (FSP_P3_PREFETCH) {
+            const int ng = g + gstride;
+            const int nit = W.find(ng < nw ? ng : g);
+            const PassArgs &b = W.item[nit];
+            const int nline = (ng - W.offs[nit]) * LPW + li;
+            const bool nact = ng < nw && nline < (b.n0 + 1) * b.rows1;
+            const float2 *L = b.buf0 + (size_t)(nact ? nline : 0) * b.n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r)
+                if (nact) pv[r] = L[j + r * T];
+        }
         const int kx = lc / a.rows1, row = lc % a.rows1;
         line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
         const float *Kr = krow(a, kx, row);
@@ -944,6 +958,76 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS, FSP_P3_MINB) p3_fwd(const
                 float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
                 for (int r = 0; r < E / 2; ++r) L1[j + r * T] = q[r];
+            }
+        }
+    }
+}
+
+// Single-solve forward middle pass (the arguments by value; same arithmetic
+// as p3_fwd below, kept separate because its register allocation is smaller).
+template <int N>
+__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE)
+{
+    using C = WarpCfg<N>;
+    constexpr int E = C::E, T = C::T, LPW = C::LPW;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int li = lane / T, j = lane % T;
+    const int n2 = a.n2;
+    const int lines = (a.n0 + 1) * a.rows1;
+    const int groups = (lines + LPW - 1) / LPW;
+    const int gstride = gridDim.x * C::WARPS;
+    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
+    int g = blockIdx.x * C::WARPS + warp;
+    float2 pv[E / 2];
+    {
+        const int line = g * LPW + li;
+        const bool act = g < groups && line < lines;
+        const float2 *L = a.buf0 + (size_t)(act ? line : 0) * n2;
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
+    }
+    for (; g < groups; g += gstride) {
+        const int line = g * LPW + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
+        {
+            const int ng = g + gstride;
+            const int nline = ng * LPW + li;
+            const bool nact = ng < groups && nline < lines;
+            const float2 *L = a.buf0 + (size_t)(nact ? nline : 0) * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r)
+                if (nact) pv[r] = L[j + r * T];
+        }
+        const int kx = lc / a.rows1, row = lc % a.rows1;
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        const float *Kr = krow(a, kx, row);
+        float2 u[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int kf = k <= n2 ? k : N - k;
+            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+            const float kk = wave(k, n2, a.k2s);
+            u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+        }
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        if (act) {
+            float2 *L0 = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+        }
+        if (withE) {
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, a.tw2, sm);
+            if (act) {
+                float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
             }
         }
     }
