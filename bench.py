@@ -105,6 +105,21 @@ def ncu_traffic(kernel, workload):
     return None
 
 
+def reduce_max(dist, x, device="cpu"):
+    """Maximum of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -249,12 +264,8 @@ def run_gpu(args):
         if dist is not None:
             dist.barrier()
 
-    def reduce_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=rho.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def reduce_max_local(x):
+        return reduce_max(dist, x, rho.device if dist is not None and dist.get_backend() == "nccl" else "cpu")
 
     for m in ("vgf", "he"):
         for _ in range(args.warmup):
@@ -286,7 +297,7 @@ def run_gpu(args):
         ms = start.elapsed_time(end)
         per_pass = [statistics.mean(evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps))
                     for i in range(npass)]
-        results[m] = {"ms": reduce_max(ms), "per_pass_ms": per_pass}
+        results[m] = {"ms": reduce_max_local(ms), "per_pass_ms": per_pass}
     clk = clocks.stop()
 
     # end to end through the public API: pinned host rho in, phi and E back to pinned host memory
@@ -312,7 +323,7 @@ def run_gpu(args):
         s1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = reduce_max(s0.elapsed_time(s1))
+        e2e_ms = reduce_max_local(s0.elapsed_time(s1))
 
     if rank != 0:
         if dist is not None:
@@ -328,7 +339,7 @@ def run_gpu(args):
     achieved = pb[dom_name] / (vgf["per_pass_ms"][dom] * 1e-3) / 1e9
     total_bytes = sum(pb.values())
     ms_step = vgf["ms"] / args.steps
-    value = ws * args.steps / (vgf["ms"] * 1e-3)
+    value = job_value(args.steps, ws, vgf["ms"])
     he_ms_step = results["he"]["ms"] / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
