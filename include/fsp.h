@@ -156,6 +156,32 @@ int fsp_plan_kernel_spectrum(const fsp_plan *plan, void *host_out, size_t bytes)
 
 void fsp_plan_destroy(fsp_plan *plan);
 
+/*
+ * fsp_solve without a workspace, for callers that cannot allocate device
+ * memory when they solve: code running while a host framework owns the
+ * allocator (plugins, callbacks, pooled applications that forbid library
+ * allocations), real-time loops whose memory is fixed at start-up, and paths
+ * that must not call cudaMalloc because it can synchronise the device.  This
+ * is a calling convention of this library; the paper has no counterpart.
+ *
+ * Same arguments, layouts and results as fsp_solve.  The scratch is one
+ * static device array of FSP_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits; the call allocates nothing (no
+ * cudaMalloc, no cudaFree, no allocating library routine).  The plan itself is
+ * created beforehand with fsp_plan_create (that call allocates, once per
+ * geometry).  A grid whose workspace (fsp_plan_workspace_bytes) exceeds the
+ * scratch returns FSP_ERR_WORKSPACE (3D cubes up to 128^3 fit).
+ *
+ * The first call on a device looks up the scratch address on that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one scratch array and it keeps the last
+ * call's contents (each solve writes every scratch element it later reads, so
+ * nothing needs clearing).  Calls that overlap on the GPU (different streams,
+ * or different plans at once) race on the scratch: serialise them.
+ */
+#define FSP_NOALLOC_SCRATCH_BYTES (80u * 1024u * 1024u)
+int fsp_solve_noalloc(fsp_plan *plan, const void *rho, void *phi, void *E, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,6 +37,7 @@ SIGNATURES = {
     "fsp_plan_set_pass_events": (_i, [_vp, _vpp, _i]),
     "fsp_plan_kernel_spectrum": (_i, [_vp, _vp, _sz]),
     "fsp_plan_destroy": (None, [_vp]),
+    "fsp_solve_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp]),
 }
 
 
