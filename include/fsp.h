@@ -148,6 +148,21 @@ void fsp_batch_destroy(fsp_batch *batch);
 int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count);
 
 /*
+ * Autotuner.  Each pass has launch variants (bit 1: 8 instead of 16 values per
+ * thread in column tiles; bit 2: one CTA per SM in persistent launches); the
+ * choice is a process-wide table keyed by pass and padded length, read by
+ * every solve.  fsp_autotune fills it for the passes this plan uses:
+ * mode 0 reads the JSON cache at cache_path (may be NULL) only; mode 1 reads
+ * it and times the missing passes on this plan's geometry; mode 2 times all
+ * of them.  With a cache_path the table is written back, keyed by GPU
+ * architecture.  This call allocates scratch buffers and synchronises (it is
+ * set-up, not a solve).  fsp_tuned_variant reports an entry: kind is 0..7 for
+ * p1_fwd, p1_adj, p2_fwd, p2_adj, p3_fwd, p3_adj, p4_fwd, p5_fwd.
+ */
+int fsp_autotune(fsp_plan *plan, const char *cache_path, int mode);
+int fsp_tuned_variant(int kind, int N);
+
+/*
  * Test hook: copy the plan's FP32 kernel spectrum to host memory, layout
  * [nx+1][ny+1][nz+1] (2D: [nx+1][ny+1]), entry (kx,ky,kz) = prod(h)/prod(2n)
  * times the DFT of the padded kernel at index k (indices k and 2n-k share it).

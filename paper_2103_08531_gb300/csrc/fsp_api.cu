@@ -335,19 +335,19 @@ int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E,
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
     int e = 0, m = 0;
     mark(p, m++, st);
-    e = launch_axis0(PASS_P1F, N0, &a, 1, st);
+    e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
     mark(p, m++, st);
     if (!e && p.three_d) {
-        e = launch_axis1(PASS_P2F, N1, &a, 1, 0, st);
+        e = launch_axis1(PASS_P2F, N1, &a, 1, 0, tuned_variant(PASS_P2F, N1), st);
         mark(p, m++, st);
     }
-    if (!e) e = launch_axis2(PASS_P3F, N2, &a, 1, withE, st);
+    if (!e) e = launch_axis2(PASS_P3F, N2, &a, 1, withE, tuned_variant(PASS_P3F, N2), st);
     mark(p, m++, st);
     if (!e && p.three_d) {
-        e = launch_axis1(PASS_P4F, N1, &a, 1, withE, st);
+        e = launch_axis1(PASS_P4F, N1, &a, 1, withE, tuned_variant(PASS_P4F, N1), st);
         mark(p, m++, st);
     }
-    if (!e) e = launch_axis0(PASS_P5F, N0, &a, 1, st);
+    if (!e) e = launch_axis0(PASS_P5F, N0, &a, 1, tuned_variant(PASS_P5F, N0), st);
     mark(p, m++, st);
     return e ? FSP_ERR_CUDA : FSP_OK;
 }
@@ -364,23 +364,23 @@ int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, f
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
     int m = 0;
     mark(p, m++, st);
-    int e = launch_axis0(PASS_P1A, N0, &a, 1, st);
+    int e = launch_axis0(PASS_P1A, N0, &a, 1, 0, st);
     mark(p, m++, st);
     if (!e && p.three_d) {
-        e = launch_axis1(PASS_P2A, N1, &a, 1, 1, st);
+        e = launch_axis1(PASS_P2A, N1, &a, 1, 1, 0, st);
         mark(p, m++, st);
     }
-    if (!e) e = launch_axis2(PASS_P3A, N2, &a, 1, 1, st);
+    if (!e) e = launch_axis2(PASS_P3A, N2, &a, 1, 1, tuned_variant(PASS_P3A, N2), st);
     mark(p, m++, st);
     if (!e && p.three_d) {
-        e = launch_axis1(PASS_P4F, N1, &a, 1, 0, st);
+        e = launch_axis1(PASS_P4F, N1, &a, 1, 0, tuned_variant(PASS_P4F, N1), st);
         mark(p, m++, st);
     }
     if (!e) {
         PassArgs b = a;
         b.out[0] = g_rho;
         b.out[1] = b.out[2] = b.out[3] = nullptr;
-        e = launch_axis0(PASS_P5F, N0, &b, 1, st);
+        e = launch_axis0(PASS_P5F, N0, &b, 1, tuned_variant(PASS_P5F, N0), st);
     }
     mark(p, m++, st);
     return e ? FSP_ERR_CUDA : FSP_OK;
@@ -432,9 +432,10 @@ static int run_launches(const std::vector<PassLaunch> &L, cudaStream_t st)
 {
     for (const PassLaunch &x : L) {
         const int n = (int)x.items.size();
-        int e = x.axis == 0 ? launch_axis0(x.kind, x.N, x.items.data(), n, st)
-                : x.axis == 1 ? launch_axis1(x.kind, x.N, x.items.data(), n, x.flag, st)
-                              : launch_axis2(x.kind, x.N, x.items.data(), n, x.flag, st);
+        const int var = tuned_variant(x.kind, x.N);
+        int e = x.axis == 0 ? launch_axis0(x.kind, x.N, x.items.data(), n, var, st)
+                : x.axis == 1 ? launch_axis1(x.kind, x.N, x.items.data(), n, x.flag, var, st)
+                              : launch_axis2(x.kind, x.N, x.items.data(), n, x.flag, var, st);
         if (e) return FSP_ERR_CUDA;
     }
     return FSP_OK;

@@ -64,16 +64,29 @@ int supported_axis0(int N)
     }
 }
 
-template <int N>
-static constexpr size_t smem_p1() { return (size_t)(N / 2 * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
-template <int N>
-static constexpr size_t smem_p5() { return (size_t)(3 * (N / 2 + 1) * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
+template <int N, int EE>
+static constexpr size_t smem_p1() { return (size_t)(N / 2 * TileCfg<N, EE>::C + TileCfg<N, EE>::EX) * sizeof(float2); }
+template <int N, int EE>
+static constexpr size_t smem_p5() { return (size_t)(3 * (N / 2 + 1) * TileCfg<N, EE>::C + TileCfg<N, EE>::EX) * sizeof(float2); }
 
 // resident CTAs per SM of the persistent kernels (set by prepare)
-template <int N, int MAXI>
+template <int N, int MAXI, int EE>
 struct Occ0 {
     static inline int p1 = 1, p5 = 1;
 };
+
+template <int N, int MAXI, int EE>
+static int prep_tiles()
+{
+    int e = 0, b1 = 0, b5 = 0;
+    e |= cudaFuncSetAttribute(p1_fwd<N, MAXI, EE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1<N, EE>());
+    e |= cudaFuncSetAttribute(p5_fwd<N, MAXI, EE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5<N, EE>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_fwd<N, MAXI, EE>, TileCfg<N, EE>::THREADS, smem_p1<N, EE>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_fwd<N, MAXI, EE>, TileCfg<N, EE>::THREADS, smem_p5<N, EE>());
+    Occ0<N, MAXI, EE>::p1 = std::max(1, b1);
+    Occ0<N, MAXI, EE>::p5 = std::max(1, b5);
+    return e;
+}
 
 template <int N, int MAXI>
 static int prep_one()
@@ -81,13 +94,7 @@ static int prep_one()
     using C = ColCfg<N>;
     int e = cudaFuncSetAttribute(p1_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if constexpr (N <= 512) {
-        e |= cudaFuncSetAttribute(p1_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1<N>());
-        e |= cudaFuncSetAttribute(p5_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5<N>());
-        int b1 = 0, b5 = 0;
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p1<N>());
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p5<N>());
-        Occ0<N, MAXI>::p1 = std::max(1, b1);
-        Occ0<N, MAXI>::p5 = std::max(1, b5);
+        e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
     } else {
         e |= cudaFuncSetAttribute(p1_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         e |= cudaFuncSetAttribute(p5_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
@@ -114,7 +121,7 @@ int prepare_axis0(int N)
 template <int N>
 static int units_p1f(const PassArgs &a)
 {
-    if constexpr (N <= 512) return a.n1 * (a.n2 / (2 * TileCfg<N>::C));
+    if constexpr (N <= 512) return a.n1 * (a.n2 / (2 * FSP_TILE_C));
     else return a.n1 * ((a.n2 / 2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
 }
 template <int N>
@@ -125,23 +132,41 @@ static int units_col(const PassArgs &a)   // (y, column tile) units of P1-adjoin
 template <int N>
 static int units_p5f(const PassArgs &a)
 {
-    if constexpr (N <= 512) return a.n1 * (a.n2 / TileCfg<N>::C);
+    if constexpr (N <= 512) return a.n1 * (a.n2 / FSP_TILE_C);
     else return units_col<N>(a);
 }
 
-template <int N>
-static int run(int kind, const PassArgs *items, int n, cudaStream_t st)
+// variant bits: 1 = 8 values per thread in the tiles (else 16); 2 = one CTA per SM
+template <int N, int EE, class Wk>
+static int tile_launch(int kind, const Wk &w, int var, cudaStream_t st)
 {
-    const int cap_sm = sm_count();
+    constexpr int MAXI = Wk::max_items;
+    const int total = w.offs[w.nitems];
+    const int sms = sm_count();
     if (kind == PASS_P1F) {
-        return chunked(items, n, units_p1f<N>, [&](auto &w) {
+        const int cap = sms * ((var & 2) ? 1 : Occ0<N, MAXI, EE>::p1);
+        p1_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p1<N, EE>(), st>>>(w);
+    } else {
+        const int cap = sms * ((var & 2) ? 1 : Occ0<N, MAXI, EE>::p5);
+        p5_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p5<N, EE>(), st>>>(w);
+    }
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
+{
+    if (kind == PASS_P1F || kind == PASS_P5F) {
+        return chunked(items, n, kind == PASS_P1F ? units_p1f<N> : units_p5f<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-            const int total = w.offs[w.nitems];
-            if constexpr (N <= 512)
-                p1_fwd<N, MAXI><<<std::min(total, cap_sm * Occ0<N, MAXI>::p1), TileCfg<N>::THREADS, smem_p1<N>(), st>>>(w);
-            else
-                p1_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
-            return (int)cudaGetLastError();
+            if constexpr (N <= 512) {
+                return (var & 1) ? tile_launch<N, 8>(kind, w, var, st) : tile_launch<N, 16>(kind, w, var, st);
+            } else {
+                const int total = w.offs[w.nitems];
+                if (kind == PASS_P1F) p1_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+                else p5_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+                return (int)cudaGetLastError();
+            }
         });
     }
     if (kind == PASS_P1A) {
@@ -151,24 +176,13 @@ static int run(int kind, const PassArgs *items, int n, cudaStream_t st)
             return (int)cudaGetLastError();
         });
     }
-    if (kind == PASS_P5F) {
-        return chunked(items, n, units_p5f<N>, [&](auto &w) {
-            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-            const int total = w.offs[w.nitems];
-            if constexpr (N <= 512)
-                p5_fwd<N, MAXI><<<std::min(total, cap_sm * Occ0<N, MAXI>::p5), TileCfg<N>::THREADS, smem_p5<N>(), st>>>(w);
-            else
-                p5_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
-            return (int)cudaGetLastError();
-        });
-    }
     return (int)cudaErrorInvalidValue;
 }
 
-int launch_axis0(int kind, int N, const PassArgs *items, int n, cudaStream_t st)
+int launch_axis0(int kind, int N, const PassArgs *items, int n, int var, cudaStream_t st)
 {
     switch (N) {
-#define X(v) case v: return run<v>(kind, items, n, st);
+#define X(v) case v: return run<v>(kind, items, n, var, st);
         FSP_AXIS0_SIZES(X)
 #undef X
     default: return (int)cudaErrorInvalidValue;

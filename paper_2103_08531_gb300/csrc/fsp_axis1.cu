@@ -64,15 +64,28 @@ int supported_axis1(int N)
     }
 }
 
-template <int N>
-static constexpr size_t smem_p2() { return (size_t)(N / 2 * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
-template <int N>
-static constexpr size_t smem_p4() { return (size_t)(2 * N * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
+template <int N, int EE>
+static constexpr size_t smem_p2() { return (size_t)(N / 2 * TileCfg<N, EE>::C + TileCfg<N, EE>::EX) * sizeof(float2); }
+template <int N, int EE>
+static constexpr size_t smem_p4() { return (size_t)(2 * N * TileCfg<N, EE>::C + TileCfg<N, EE>::EX) * sizeof(float2); }
 
-template <int N, int MAXI>
+template <int N, int MAXI, int EE>
 struct Occ1 {
     static inline int p2 = 1, p4 = 1;
 };
+
+template <int N, int MAXI, int EE>
+static int prep_tiles()
+{
+    int e = 0, b2 = 0, b4 = 0;
+    e |= cudaFuncSetAttribute(p2_fwd<N, MAXI, EE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2<N, EE>());
+    e |= cudaFuncSetAttribute(p4_fwd<N, MAXI, EE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4<N, EE>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_fwd<N, MAXI, EE>, TileCfg<N, EE>::THREADS, smem_p2<N, EE>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_fwd<N, MAXI, EE>, TileCfg<N, EE>::THREADS, smem_p4<N, EE>());
+    Occ1<N, MAXI, EE>::p2 = std::max(1, b2);
+    Occ1<N, MAXI, EE>::p4 = std::max(1, b4);
+    return e;
+}
 
 template <int N, int MAXI>
 static int prep_one()
@@ -80,13 +93,7 @@ static int prep_one()
     using C = ColCfg<N>;
     int e = cudaFuncSetAttribute(p2_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if constexpr (N <= 512) {
-        e |= cudaFuncSetAttribute(p2_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2<N>());
-        e |= cudaFuncSetAttribute(p4_fwd<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4<N>());
-        int b2 = 0, b4 = 0;
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p2<N>());
-        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_fwd<N, MAXI>, TileCfg<N>::THREADS, smem_p4<N>());
-        Occ1<N, MAXI>::p2 = std::max(1, b2);
-        Occ1<N, MAXI>::p4 = std::max(1, b4);
+        e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
     } else {
         e |= cudaFuncSetAttribute(p2_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         e |= cudaFuncSetAttribute(p4_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
@@ -113,7 +120,7 @@ int prepare_axis1(int N)
 template <int N>
 static int units_tile(const PassArgs &a)   // (k0, column tile) units
 {
-    if constexpr (N <= 512) return (a.n0 + 1) * (a.n2 / TileCfg<N>::C);
+    if constexpr (N <= 512) return (a.n0 + 1) * (a.n2 / FSP_TILE_C);
     else return (a.n0 + 1) * ((a.n2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
 }
 template <int N>
@@ -122,19 +129,37 @@ static int units_blk(const PassArgs &a)
     return (a.n0 + 1) * ((a.n2 + ColCfg<N>::BZ - 1) / ColCfg<N>::BZ);
 }
 
-template <int N>
-static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st)
+// variant bits: 1 = 8 values per thread in the tiles (else 16); 2 = one CTA per SM
+template <int N, int EE, class Wk>
+static int tile_launch(int kind, const Wk &w, int flag, int var, cudaStream_t st)
 {
-    const int cap_sm = sm_count();
+    constexpr int MAXI = Wk::max_items;
+    const int total = w.offs[w.nitems];
+    const int sms = sm_count();
     if (kind == PASS_P2F) {
+        const int cap = sms * ((var & 2) ? 1 : Occ1<N, MAXI, EE>::p2);
+        p2_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p2<N, EE>(), st>>>(w);
+    } else {
+        const int cap = sms * ((var & 2) ? 1 : Occ1<N, MAXI, EE>::p4);
+        p4_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p4<N, EE>(), st>>>(w, flag);
+    }
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
+{
+    if (kind == PASS_P2F || kind == PASS_P4F) {
         return chunked(items, n, units_tile<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-            const int total = w.offs[w.nitems];
-            if constexpr (N <= 512)
-                p2_fwd<N, MAXI><<<std::min(total, cap_sm * Occ1<N, MAXI>::p2), TileCfg<N>::THREADS, smem_p2<N>(), st>>>(w);
-            else
-                p2_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
-            return (int)cudaGetLastError();
+            if constexpr (N <= 512) {
+                return (var & 1) ? tile_launch<N, 8>(kind, w, flag, var, st) : tile_launch<N, 16>(kind, w, flag, var, st);
+            } else {
+                const int total = w.offs[w.nitems];
+                if (kind == PASS_P2F) p2_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+                else p4_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w, flag);
+                return (int)cudaGetLastError();
+            }
         });
     }
     if (kind == PASS_P2A) {
@@ -144,25 +169,13 @@ static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st
             return (int)cudaGetLastError();
         });
     }
-    if (kind == PASS_P4F) {
-        return chunked(items, n, units_tile<N>, [&](auto &w) {
-            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-            const int total = w.offs[w.nitems];
-            if constexpr (N <= 512)
-                p4_fwd<N, MAXI><<<std::min(total, cap_sm * Occ1<N, MAXI>::p4), TileCfg<N>::THREADS, smem_p4<N>(), st>>>(w,
-                                                                                                                   flag);
-            else
-                p4_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w, flag);
-            return (int)cudaGetLastError();
-        });
-    }
     return (int)cudaErrorInvalidValue;
 }
 
-int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st)
+int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     switch (N) {
-#define X(v) case v: return run<v>(kind, items, n, flag, st);
+#define X(v) case v: return run<v>(kind, items, n, flag, var, st);
         FSP_AXIS1_SIZES(X)
 #undef X
     default: return (int)cudaErrorInvalidValue;

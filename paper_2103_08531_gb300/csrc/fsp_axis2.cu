@@ -121,7 +121,7 @@ static int units_p3(const PassArgs &a)
 }
 
 template <int N>
-static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st)
+static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     const int cap_sm = sm_count();
     return chunked(items, n, units_p3<N>, [&](auto &w) {
@@ -130,12 +130,17 @@ static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st
         if constexpr (N <= 512) {
             using C = WarpCfg<N>;
             const int ctas = (total + C::WARPS - 1) / C::WARPS;
+            // variant bit 2: one CTA per SM (else as many as fit)
+            const bool one = (var & 2) != 0;
             if (kind == PASS_P3F && MAXI == 1)
-                p3_fwd1<N><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3one), C::THREADS, C::SMEM, st>>>(w.item[0], flag);
+                p3_fwd1<N><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3one)), C::THREADS, C::SMEM, st>>>(
+                    w.item[0], flag);
             else if (kind == PASS_P3F)
-                p3_fwd<N, MAXI><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3), C::THREADS, C::SMEM, st>>>(w, flag);
+                p3_fwd<N, MAXI><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3)), C::THREADS, C::SMEM, st>>>(
+                    w, flag);
             else
-                p3_adj<N, MAXI><<<std::min(ctas, cap_sm * Occ2<N, MAXI>::p3a), C::THREADS, C::SMEM, st>>>(w, flag);
+                p3_adj<N, MAXI><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3a)), C::THREADS, C::SMEM, st>>>(
+                    w, flag);
         } else {
             using C = RowCfg<N>;
             if (kind == PASS_P3F) p3_fwd_blk<N, MAXI><<<total, C::THREADS, C::SMEM, st>>>(w, flag);
@@ -145,11 +150,11 @@ static int run(int kind, const PassArgs *items, int n, int flag, cudaStream_t st
     });
 }
 
-int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st)
+int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     if (kind != PASS_P3F && kind != PASS_P3A) return (int)cudaErrorInvalidValue;
     switch (N) {
-#define X(v) case v: return run<v>(kind, items, n, flag, st);
+#define X(v) case v: return run<v>(kind, items, n, flag, var, st);
         FSP_AXIS2_SIZES(X)
 #undef X
     default: return (int)cudaErrorInvalidValue;

@@ -52,9 +52,15 @@ int supported_axis2(int N);
 int prepare_axis0(int N);
 int prepare_axis1(int N);
 int prepare_axis2(int N);
-int launch_axis0(int kind, int N, const PassArgs *items, int n, cudaStream_t st);
-int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st);
-int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, cudaStream_t st);
+// var: tuning variant bits (1 = 8 values per thread in column tiles, 2 = one
+// CTA per SM in persistent launches); chosen by the autotuner (fsp_autotune.cu).
+int launch_axis0(int kind, int N, const PassArgs *items, int n, int var, cudaStream_t st);
+int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
+int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
+
+// fsp_autotune.cu: the variant chosen for a pass kind at padded length N (0 if untuned)
+int tuned_variant(int kind, int N);
+constexpr int PASS_KINDS = 8;
 
 } // namespace fsp
 

@@ -556,9 +556,6 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
 // while the current one is transformed, so loads overlap the arithmetic.
 // =====================================================================
 
-#ifndef FSP_TILE_E
-#define FSP_TILE_E 16
-#endif
 #ifndef FSP_TILE_C
 #define FSP_TILE_C 16
 #endif
@@ -573,13 +570,14 @@ struct TilePlan<N, 8> {
     using R = typename Plan1D<N>::R;
 };
 
-template <int N>
+// EE = 16: 16 values per thread (Plan16); EE = 8: Plan1D (8 per thread, 12 for 192).
+template <int N, int EE = 16>
 struct TileCfg {
-    static constexpr int E = TilePlan<N, FSP_TILE_E>::E;
+    static constexpr int E = TilePlan<N, EE>::E;
     static constexpr int T = N / E;
     static constexpr int C = FSP_TILE_C;           // columns per tile (complex)
     static constexpr int THREADS = T * C;
-    using RAD = typename TilePlan<N, FSP_TILE_E>::R;
+    using RAD = typename TilePlan<N, EE>::R;
     static constexpr int EX = N * C;                // exchange buffer, float2
 };
 
@@ -598,10 +596,10 @@ __device__ __forceinline__ void issue_rows(float2 *dst, const void *src, size_t 
 
 // P1: rho pairs (z, z+1) -> half spectrum in k0, output rows 0..n1-1 of buf1
 // (3D) or buf0 (2D).  Unit: (y, tile of 2C reals of axis 2).
-template <int N, int MAXI>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(const __grid_constant__ Work<MAXI> W)
+template <int N, int MAXI, int EE>
+__global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p1_fwd(const __grid_constant__ Work<MAXI> W)
 {
-    using C = TileCfg<N>;
+    using C = TileCfg<N, EE>;
     constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
@@ -655,10 +653,10 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_fwd(const __grid_const
 }
 
 // P2: buf1 rows 0..n1-1 -> forward axis 1 -> buf0 rows 0..2n1-1.  Unit: (k0, tile of C columns).
-template <int N, int MAXI>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(const __grid_constant__ Work<MAXI> W)
+template <int N, int MAXI, int EE>
+__global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p2_fwd(const __grid_constant__ Work<MAXI> W)
 {
-    using C = TileCfg<N>;
+    using C = TileCfg<N, EE>;
     constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
@@ -697,10 +695,10 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_fwd(const __grid_const
 
 // P4: buf0 (phi stream, 2 n1 rows) -> rows [0,n1) phi, rows [n1,2n1) -i k1 phi;
 // buf1 (E2 stream) -> rows [0,n1).  Unit: (k0, tile of C columns).
-template <int N, int MAXI>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(const __grid_constant__ Work<MAXI> W, int withE)
+template <int N, int MAXI, int EE>
+__global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p4_fwd(const __grid_constant__ Work<MAXI> W, int withE)
 {
-    using C = TileCfg<N>;
+    using C = TileCfg<N, EE>;
     constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T;
     using RAD = typename C::RAD;
@@ -757,10 +755,10 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p4_fwd(const __grid_const
 }
 
 // P5: half spectra in k0 -> real outputs (see the header comment).  Unit: (y, tile of C columns).
-template <int N, int MAXI>
-__global__ void __launch_bounds__(TileCfg<N>::THREADS) p5_fwd(const __grid_constant__ Work<MAXI> W)
+template <int N, int MAXI, int EE>
+__global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_constant__ Work<MAXI> W)
 {
-    using C = TileCfg<N>;
+    using C = TileCfg<N, EE>;
     constexpr int CC = C::C;
     constexpr int E = C::E, T = C::T, NH = N / 2, ROWS = N / 2 + 1;
     using RAD = typename C::RAD;

@@ -7,6 +7,7 @@ kernels on the caller's current torch stream.  PyTorch provides device memory
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -55,6 +56,15 @@ class Plan:
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             _lib.check(self.lib.fsp_plan_set_workspace(self.handle, _ptr(self.workspace), nbytes),
                        "fsp_plan_set_workspace")
+            mode = os.environ.get("FSP_AUTOTUNE", "off")
+            if mode in ("cached", "full", "retune"):
+                self.autotune(os.environ.get("FSP_TUNE_CACHE"), {"cached": 0, "full": 1, "retune": 2}[mode])
+
+    def autotune(self, cache_path=None, mode: int = 1):
+        """Pick launch variants for this plan's passes (see fsp_autotune in include/fsp.h)."""
+        path = None if cache_path is None else str(cache_path).encode()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.fsp_autotune(self.handle, path, int(mode)), "fsp_autotune")
 
     # ----------------------------------------------------------------- info
     def geometry(self) -> dict:
@@ -136,6 +146,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+PASS_KINDS = ["p1_fwd", "p1_adj", "p2_fwd", "p2_adj", "p3_fwd", "p3_adj", "p4_fwd", "p5_fwd"]
+
+
+def tuned_variant(kind: str, N: int) -> int:
+    """Current autotuner choice for a pass at padded length N."""
+    return _lib.load().fsp_tuned_variant(PASS_KINDS.index(kind), int(N))
 
 
 def _arr(ptrs):

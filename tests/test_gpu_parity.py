@@ -262,6 +262,65 @@ def test_batched_rejects_repeated_plan(fsp):
         fsp.solve_batched([p, p], [r, r])
 
 
+# --------------------------------------------------------------- autotuner
+
+def _write_cache(path, arch, shape, var_tile, var_p3):
+    d = len(shape)
+    Ns = {"p1_fwd": 2 * shape[0], "p5_fwd": 2 * shape[0], "p3_fwd": 2 * shape[-1]}
+    if d == 3:
+        Ns.update({"p2_fwd": 2 * shape[1], "p4_fwd": 2 * shape[1]})
+    entries = {f"{k}/{N}": (var_p3 if k == "p3_fwd" else var_tile) for k, N in Ns.items()}
+    import json
+    with open(path, "w") as f:
+        json.dump({arch: entries}, f)
+
+
+@pytest.mark.parametrize("shape,h", [((64, 64, 32), (0.02, 0.025, 0.03)), ((32, 128, 64), (0.03, 0.01, 0.02)),
+                                     ((128, 64), (0.01, 0.02))])
+def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
+    """Each launch variant the autotuner can pick gives the oracle's answer."""
+    cap = torch.cuda.get_device_capability()
+    arch = f"sm_{cap[0] * 10 + cap[1]}"
+    prob = _mixture(shape, h, seed=61)
+    rho32 = prob.rho(np.float32)
+    rho = torch.from_numpy(rho32).cuda()
+    plan = fsp.Plan(shape, h, "vgf")
+    g = oracle_mod.kernel_vgf(list(shape), h)
+    p_ref, E_ref = oracle_mod.solve_with_kernel(g, rho32.astype(np.float64), h)
+    path = str(tmp_path / "tune.json")
+    try:
+        for vt, vp in [(0, 0), (1, 0), (2, 2), (3, 2)]:
+            _write_cache(path, arch, shape, vt, vp)
+            plan.autotune(path, 0)
+            assert fsp.tuned_variant("p1_fwd", 2 * shape[0]) == vt
+            phi, E = plan.solve(rho)
+            assert rel(phi.cpu(), p_ref) <= TOL and rel(E.cpu(), E_ref) <= TOL, (vt, vp)
+    finally:
+        _write_cache(path, arch, shape, 0, 0)
+        plan.autotune(path, 0)
+
+
+def test_autotune_measures_and_writes_cache(fsp, tmp_path):
+    import json
+    shape, h = (64, 64, 64), (0.02, 0.02, 0.02)
+    plan = fsp.Plan(shape, h, "vgf")
+    rho = torch.from_numpy(_mixture(shape, h, seed=62).rho(np.float32)).cuda()
+    phi0, E0 = plan.solve(rho)
+    path = tmp_path / "tune.json"
+    plan.autotune(path, 2)
+    data = json.load(open(path))
+    (arch, entries), = data.items()
+    assert arch.startswith("sm_")
+    assert set(entries) == {"p1_fwd/128", "p2_fwd/128", "p3_fwd/128", "p4_fwd/128", "p5_fwd/128"}
+    phi1, E1 = plan.solve(rho)
+    assert rel(phi1.cpu(), phi0.cpu()) <= TOL and rel(E1.cpu(), E0.cpu()) <= TOL
+    # reset the process-wide table for the remaining tests
+    for k in entries:
+        entries[k] = 0
+    json.dump({arch: entries}, open(path, "w"))
+    plan.autotune(path, 0)
+
+
 # ------------------------------------------------------------ full sizes
 
 def test_full_size_256_vgf_against_oracle(fsp, oracle_mod):
