@@ -90,7 +90,10 @@ static int prep_one()
         Occ2<N, MAXI>::p3a = std::max(1, ba);
     } else {
         using C = RowCfg<N>;
-        e |= cudaFuncSetAttribute(p3_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        e |= cudaFuncSetAttribute(p3_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_STAGED);
+        int b = 0;
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd_blk<N, MAXI>, C::THREADS, C::SMEM_STAGED);
+        Occ2<N, MAXI>::p3 = std::max(1, b);
         e |= cudaFuncSetAttribute(p3_adj_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     }
     return e;
@@ -143,7 +146,9 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
                     w, flag);
         } else {
             using C = RowCfg<N>;
-            if (kind == PASS_P3F) p3_fwd_blk<N, MAXI><<<total, C::THREADS, C::SMEM, st>>>(w, flag);
+            if (kind == PASS_P3F)
+                p3_fwd_blk<N, MAXI><<<std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::p3)), C::THREADS,
+                                      C::SMEM_STAGED, st>>>(w, flag);
             else p3_adj_blk<N, MAXI><<<total, C::THREADS, C::SMEM, st>>>(w, flag);
         }
         return (int)cudaGetLastError();

@@ -90,13 +90,26 @@ constexpr int BATCH_MAX = 32;   // items per batched launch
     const PassArgs &a = (W).item[it_##u];     \
     const int u = (w) - (W).offs[it_##u]
 
+// Block-synchronous column tiles (lengths above 512, and the adjoint entry
+// passes).  With 16 columns the exchange buffer is row-major [pos][col] (a
+// half-warp covers one 128-byte row: conflict-free); narrower tiles, forced by
+// long lines, store each column contiguously with one padding slot per 16
+// positions, which keeps their Stockham exchanges conflict-free too.
 template <int N>
 struct ColCfg {
     static constexpr int E = Plan1D<N>::E;
     static constexpr int T = N / E;
     static constexpr int BZ = (T * 16 <= 1024) ? 16 : (1024 / T);
     static constexpr int THREADS = T * BZ;
-    static constexpr size_t SMEM = (size_t)N * BZ * sizeof(float2);
+    static constexpr bool WIDE = BZ >= 16;
+    static constexpr int SPAN = RowSpan<N, 4>::value;   // per-column span when !WIDE
+    static constexpr size_t SMEM = (size_t)(WIDE ? N * BZ : SPAN * BZ) * sizeof(float2);
+    using View = typename std::conditional<WIDE, ColView, RowView<4>>::type;
+    static __device__ __forceinline__ View view(float2 *smem, int col)
+    {
+        if constexpr (WIDE) return ColView{smem + col, BZ};
+        else return RowView<4>{smem + col * SPAN};
+    }
 };
 
 template <int N>
@@ -108,6 +121,11 @@ struct RowCfg {
     static constexpr int PAD = 4;
     static constexpr int SPAN = RowSpan<N, PAD>::value;
     static constexpr size_t SMEM = (size_t)SPAN * LPC * sizeof(float2);
+    // 512-thread lines (2 n >= 4096) keep the product spectrum in shared memory
+    // instead of a second register array (the registers would spill)
+    static constexpr bool SAVE = T >= 256;
+    static constexpr size_t SMEM_STAGED =
+        SMEM + (size_t)LPC * (N / 2) * sizeof(float2) + (SAVE ? (size_t)LPC * N * sizeof(float2) : 0);
 };
 
 // ----------------------------------------------------------------- P1 (axis 0)
@@ -134,7 +152,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_blk(const __grid_co
         v[r] = make_float2(0.f, 0.f);
         if (r < E / 2 && act) v[r] = __ldg(reinterpret_cast<const float2 *>(rho + gidx(a, j + r * T, y, z0)));
     }
-    ColView sm{smem + col, BZ};
+    const auto sm = C::view(smem, col);
     line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
 #pragma unroll
     for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
@@ -174,7 +192,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_adj(const __grid_consta
     const bool act = z < a.n2;
     const float *gp = a.in[0], *g0 = a.in[1], *g1 = a.in[2], *g2 = a.in[3];
     const bool hasE = g0 != nullptr;
-    ColView sm{smem + col, BZ};
+    const auto sm = C::view(smem, col);
     constexpr int NH = N / 2;
     for (int pass = 0; pass < (hasE ? 2 : 1); ++pass) {
         const float *re = pass == 0 ? gp : g1;
@@ -241,7 +259,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_fwd_blk(const __grid_co
         v[r] = make_float2(0.f, 0.f);
         if (r < E / 2 && act) v[r] = src[iidx(a, kx, j + r * T, z)];
     }
-    line_fft<N, E, false, true, RAD>(v, j, a.tw1, ColView{smem + col, BZ});
+    line_fft<N, E, false, true, RAD>(v, j, a.tw1, C::view(smem, col));
     if (act) {
 #pragma unroll
         for (int r = 0; r < E; ++r) dst[iidx(a, kx, j + r * T, z)] = v[r];
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p2_adj(const __grid_consta
     const int z = (u % xt) * BZ + col;
     const bool act = z < a.n2;
     const int n1 = a.n1;
-    ColView sm{smem + col, BZ};
+    const auto sm = C::view(smem, col);
     float2 v[E], w[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -316,54 +334,108 @@ __device__ __forceinline__ const float *krow(const PassArgs &a, int kx, int row)
 
 // Forward: line of buf0 -> F2 -> x K -> inverse -> buf0 (phi stream), and
 // -i k2 K -> inverse -> buf1 (E2 stream) when withE.
+// Long lines (2 n2 >= 1024): LPC lines per CTA, persistent over line groups;
+// the next group's pruned input (LPC x n2 contiguous complex) is copied into
+// shared memory with cp.async while the current group is transformed.
 template <int N, int MAXI>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_constant__ Work<MAXI> W, int withE)
 {
     using C = RowCfg<N>;
-    constexpr int E = C::E, T = C::T, LPC = C::LPC;
+    constexpr int E = C::E, T = C::T, LPC = C::LPC, NH = N / 2;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
+    float2 *stage = smem + C::SPAN * LPC;   // LPC x NH complex
     const int li = threadIdx.x / T, j = threadIdx.x % T;
-    FSP_UNIT(W, blockIdx.x, a, u);
-    const int lines = (a.n0 + 1) * a.rows1;
-    const int line = u * LPC + li;
-    const bool act = line < lines;
-    const int lc = act ? line : 0;
-    const int kx = lc / a.rows1, row = lc % a.rows1;
-    const int n2 = a.n2;
-    float2 *L0 = a.buf0 + (size_t)lc * n2;
-    float2 *L1 = a.buf1 + (size_t)lc * n2;
+    const int nw = W.count();
     RowView<C::PAD> sm{smem + li * C::SPAN};
-    float2 v[E];
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const int lines = (b.n0 + 1) * b.rows1;
+        const int first = ub * LPC;
+        const int cnt = min(LPC, lines - first);
+        const float2 *src = b.buf0 + (size_t)first * b.n2;   // cnt contiguous lines
+        const int chunks = cnt * NH / 2;                      // 16-byte chunks
+        for (int c = threadIdx.x; c < chunks; c += C::THREADS) cp_async16(stage + 2 * c, src + 2 * c);
+    };
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
+    cp_async_commit();
+    for (; w < nw; w += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        FSP_UNIT(W, w, a, u);
+        const int lines = (a.n0 + 1) * a.rows1;
+        const int line = u * LPC + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
+        const int kx = lc / a.rows1, row = lc % a.rows1;
+        const int n2 = a.n2;
+        float2 v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        v[r] = make_float2(0.f, 0.f);
-        if (r < E / 2 && act) v[r] = L0[j + r * T];
-    }
-    line_fft<N, E, false, true, RAD>(v, j, a.tw2, sm);
-    const float *Kr = krow(a, kx, row);
-    float2 q[E];
+        for (int r = 0; r < E; ++r) v[r] = (r < E / 2 && act) ? stage[li * NH + j + r * T] : make_float2(0.f, 0.f);
+        __syncthreads();
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
+        cp_async_commit();
+        line_fft<N, E, false, true, RAD>(v, j, a.tw2, sm);
+        const float *Kr = krow(a, kx, row);
+        if constexpr (C::SAVE) {
+            float2 *sv = stage + LPC * NH + li * N;   // product spectrum of this line
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int k = j + r * T;
-        const int kf = k <= n2 ? k : N - k;
-        const float kv = act ? __ldg(Kr + kf) : 0.f;
-        v[r] = kv * v[r];
-        const float kk = wave(k, n2, a.k2s);
-        q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
-    }
-    line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
-    if (act) {
+            for (int r = 0; r < E; ++r) {
+                const int k = j + r * T;
+                const int kf = k <= n2 ? k : N - k;
+                v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+                sv[k] = v[r];
+            }
+            line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+            if (act) {
+                float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
-        for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
-    }
-    if (withE) {
-        line_fft<N, E, true, false, RAD>(q, j, a.tw2, sm);
-        if (act) {
+                for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+            }
+            if (withE) {
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) L1[j + r * T] = q[r];
+                for (int r = 0; r < E; ++r) {
+                    const int k = j + r * T;
+                    const float kk = wave(k, n2, a.k2s);
+                    const float2 sk = sv[k];
+                    v[r] = make_float2(kk * sk.y, -kk * sk.x);   // -i k2 (K rho^)
+                }
+                line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+                if (act) {
+                    float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                    for (int r = 0; r < E / 2; ++r) L1[j + r * T] = v[r];
+                }
+            }
+        } else {
+            float2 q[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int k = j + r * T;
+                const int kf = k <= n2 ? k : N - k;
+                const float kv = act ? __ldg(Kr + kf) : 0.f;
+                v[r] = kv * v[r];
+                const float kk = wave(k, n2, a.k2s);
+                q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
+            }
+            line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+            if (act) {
+                float2 *L0 = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+                for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+            }
+            if (withE) {
+                line_fft<N, E, true, false, RAD>(q, j, a.tw2, sm);
+                if (act) {
+                    float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                    for (int r = 0; r < E / 2; ++r) L1[j + r * T] = q[r];
+                }
+            }
         }
     }
+    cp_async_wait_all();
 }
 
 // Adjoint: buf0 line V (and buf1 line Z when hasE) -> K (F2 V + i k2 F2 Z) -> inverse -> buf0.
@@ -439,7 +511,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p4_fwd_blk(const __grid_co
     const bool act = z < a.n2;
     const int zc = act ? z : 0;
     const int n1 = a.n1;
-    ColView sm{smem + col, BZ};
+    const auto sm = C::view(smem, col);
     float2 v[E], q[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -489,7 +561,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
     const int zc = act ? z : 0;
     constexpr int NH = N / 2;
     float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
-    ColView sm{smem + col, BZ};
+    const auto sm = C::view(smem, col);
     if (phi || e0) {
         float2 v[E];
 #pragma unroll

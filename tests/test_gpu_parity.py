@@ -107,6 +107,26 @@ def test_solve_parity(fsp, oracle_mod, method, name, shape, h):
         assert rel(E[a], E_ref[a]) <= 4 * TOL
 
 
+LONG = [
+    ("z1024", (32, 32, 512), (0.03, 0.03, 0.004), "vgf"),     # middle pass on 1024-point lines
+    ("y4096", (64, 2048), (0.01, 0.001), "he"),                # 2D, 4096-point middle lines
+    ("y8192", (32, 4096), (0.02, 0.0005), "he"),               # 2D, 8192-point middle lines
+    ("x4096", (2048, 64), (0.001, 0.01), "he"),                # 2D, 4096-point column tiles (narrow)
+    ("x8192", (4096, 32), (0.0005, 0.02), "he"),               # 2D, 8192-point column tiles (narrow)
+]
+
+
+@pytest.mark.parametrize("name,shape,h,method", LONG)
+def test_solve_parity_long_lines(fsp, oracle_mod, name, shape, h, method):
+    """The block-synchronous passes for 1024- to 8192-point lines against the oracle."""
+    prob = _mixture(shape, h, seed=len(name))
+    plan, rho32, phi, E = gpu_solve(fsp, prob, method)
+    g = oracle_mod.kernel(method, list(shape), h)
+    p_ref, E_ref = oracle_mod.solve_with_kernel(g, rho32.astype(np.float64), h)
+    assert rel(phi, p_ref) <= TOL
+    assert rel(E, E_ref) <= TOL
+
+
 @pytest.mark.parametrize("name,shape,h", SMALL[:2] + SMALL[3:4])
 def test_phi_only_and_E_only(fsp, name, shape, h):
     prob = _mixture(shape, h, seed=5)
