@@ -124,8 +124,11 @@ struct RowCfg {
     // 512-thread lines (2 n >= 4096) keep the product spectrum in shared memory
     // instead of a second register array (the registers would spill)
     static constexpr bool SAVE = T >= 256;
-    static constexpr size_t SMEM_STAGED =
-        SMEM + (size_t)LPC * (N / 2) * sizeof(float2) + (SAVE ? (size_t)LPC * N * sizeof(float2) : 0);
+    // cp.async stage after the exchange lines, rounded up to a 16-byte boundary
+    static constexpr int STAGE_OFF = (SPAN * LPC + 1) / 2 * 2;   // in float2
+    static_assert((STAGE_OFF * sizeof(float2)) % 16 == 0, "cp.async stage must be 16-byte aligned");
+    static constexpr size_t SMEM_STAGED = (size_t)STAGE_OFF * sizeof(float2) + (size_t)LPC * (N / 2) * sizeof(float2) +
+                                          (SAVE ? (size_t)LPC * N * sizeof(float2) : 0);
 };
 
 // ----------------------------------------------------------------- P1 (axis 0)
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
     constexpr int E = C::E, T = C::T, LPC = C::LPC, NH = N / 2;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
-    float2 *stage = smem + C::SPAN * LPC;   // LPC x NH complex
+    float2 *stage = smem + C::STAGE_OFF;   // LPC x NH complex, 16-byte aligned
     const int li = threadIdx.x / T, j = threadIdx.x % T;
     const int nw = W.count();
     RowView<C::PAD> sm{smem + li * C::SPAN};
