@@ -97,7 +97,6 @@ static void plan_free(Plan &p)
     if (p.tw1 != p.tw0) cudaFree(p.tw1);
     if (p.tw2 != p.tw0 && p.tw2 != p.tw1) cudaFree(p.tw2);
     cudaFree(p.K);
-    cudaFree(p.twh);
 }
 
 extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, double hy, double hz, int method,
@@ -193,10 +192,6 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
         if (rc == FSP_OK && p.tw2 != p.tw0 && p.tw2 != p.tw1 &&
             (make_twiddles(p.tw2, N2, st) || make_twiddles_aux(p.tw2, N2, st)))
             rc = FSP_ERR_CUDA;
-    }
-    if (rc == FSP_OK && dim == 2 && (N0 == 8192 || N2 == 8192)) {
-        if (cudaMalloc(&p.twh, sizeof(float2) * (4096 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
-        else if (make_twiddles(p.twh, 4096, st)) rc = FSP_ERR_CUDA;
     }
     if (rc == FSP_OK) rc = build_kernel_spectrum(&p, st);
     if (st) cudaStreamDestroy(st);
@@ -303,7 +298,6 @@ static PassArgs base_args(const Plan &p, void *ws)
     a.tw0 = p.tw0;
     a.tw1 = p.tw1;
     a.tw2 = p.tw2;
-    a.twh = p.twh;
     a.K = p.K;
     a.buf0 = reinterpret_cast<float2 *>(ws);
     a.buf1 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + align_up(p.buf_elems * sizeof(float2), 256));

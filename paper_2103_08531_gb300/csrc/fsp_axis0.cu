@@ -98,12 +98,6 @@ static int prep_one()
     } else {
         e |= cudaFuncSetAttribute(p1_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         e |= cudaFuncSetAttribute(p5_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if constexpr (N == SplitCfg::NF) {
-            e |= cudaFuncSetAttribute(p1_fwd_split<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SplitCfg::SMEM_COL);
-            e |= cudaFuncSetAttribute(p5_fwd_split<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SplitCfg::SMEM_COL);
-        }
     }
     return e;
 }
@@ -159,26 +153,9 @@ static int tile_launch(int kind, const Wk &w, int var, cudaStream_t st)
     return (int)cudaGetLastError();
 }
 
-// 8192-point lines (2D): units = (tile of SplitCfg::BZ columns or column pairs, parity)
-static int units_p1_split(const PassArgs &a) { return 2 * ((a.n2 / 2 + SplitCfg::BZ - 1) / SplitCfg::BZ); }
-static int units_p5_split(const PassArgs &a) { return 2 * ((a.n2 + SplitCfg::BZ - 1) / SplitCfg::BZ); }
-
 template <int N>
 static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
 {
-    if constexpr (N == SplitCfg::NF) {
-        if (kind == PASS_P1F || kind == PASS_P5F) {
-            return chunked(items, n, kind == PASS_P1F ? units_p1_split : units_p5_split, [&](auto &w) {
-                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-                const int total = w.offs[w.nitems];
-                if (kind == PASS_P1F)
-                    p1_fwd_split<MAXI><<<total, SplitCfg::T * SplitCfg::BZ, SplitCfg::SMEM_COL, st>>>(w);
-                else
-                    p5_fwd_split<MAXI><<<total, SplitCfg::T * SplitCfg::BZ, SplitCfg::SMEM_COL, st>>>(w);
-                return (int)cudaGetLastError();
-            });
-        }
-    }
     if (kind == PASS_P1F || kind == PASS_P5F) {
         return chunked(items, n, kind == PASS_P1F ? units_p1f<N> : units_p5f<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;

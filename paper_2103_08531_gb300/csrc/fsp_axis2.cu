@@ -95,9 +95,6 @@ static int prep_one()
         e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd_blk<N, MAXI>, C::THREADS, C::SMEM_STAGED);
         Occ2<N, MAXI>::p3 = std::max(1, b);
         e |= cudaFuncSetAttribute(p3_adj_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if constexpr (N == SplitCfg::NF)
-            e |= cudaFuncSetAttribute(p3_fwd_split<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SplitCfg::SMEM_ROW);
     }
     return e;
 }
@@ -126,20 +123,9 @@ static int units_p3(const PassArgs &a)
     else return (lines + RowCfg<N>::LPC - 1) / RowCfg<N>::LPC;
 }
 
-static int units_p3_split(const PassArgs &a) { return 2 * (a.n0 + 1) * a.rows1; }
-
 template <int N>
 static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
-    if constexpr (N == SplitCfg::NF) {
-        if (kind == PASS_P3F) {
-            return chunked(items, n, units_p3_split, [&](auto &w) {
-                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-                p3_fwd_split<MAXI><<<w.offs[w.nitems], SplitCfg::T, SplitCfg::SMEM_ROW, st>>>(w, flag);
-                return (int)cudaGetLastError();
-            });
-        }
-    }
     const int cap_sm = sm_count();
     return chunked(items, n, units_p3<N>, [&](auto &w) {
         constexpr int MAXI = std::decay_t<decltype(w)>::max_items;

@@ -24,7 +24,6 @@ struct Plan {
     int n0, n1, n2, rows1, three_d;
     float k0s, k1s, k2s;
     float2 *tw0, *tw1, *tw2;  // device twiddle tables for 2 n0, 2 n1, 2 n2
-    float2 *twh;              // 4096-point table when a 2D axis has 8192-point lines (else null)
     float *K;                 // device FP32 kernel octant
     size_t K_count;
     size_t buf_elems;         // complex elements of one intermediate buffer

@@ -23,7 +23,6 @@
 #pragma once
 
 #include "fsp_fft.cuh"
-#include <cooperative_groups.h>
 #include <stdint.h>
 #include <type_traits>
 
@@ -35,7 +34,6 @@ struct PassArgs {
     int three_d;      // 1: axis 1 is transformed
     float k0s, k1s, k2s;   // 2 pi / (2 n_a h_a)
     const float2 *tw0, *tw1, *tw2;
-    const float2 *twh;   // 4096-point table for the split 8192-point lines of 2D plans (else null)
     const float *K;   // [n0 + 1][n1 + 1 (3D) or 1][n2 + 1]
     float2 *buf0, *buf1;
     const float *in[4];
@@ -1156,207 +1154,6 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
         if (act) {
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
-        }
-    }
-}
-
-// =====================================================================
-// 2D lines of 8192 points, split by frequency parity.  The padded line has
-// its upper half zero, so X[2k' + r] = sum_{n<4096} x[n] W_8192^{r n} W_4096^{n k'}:
-// the two parities r are independent 4096-point transforms of the same input
-// (pre-twiddled for r = 1).  The cropped inverse is the sum of the parities,
-// x[n] = sum_r W_8192^{-r n} IFFT_4096(X[2k'+r])[n], n < 4096, so the two
-// CTAs of a 2-CTA cluster each invert one parity and add the partner's half
-// through distributed shared memory.  Each CTA then holds 4096-point lines,
-// which lets the column tiles be 4 columns wide.
-// =====================================================================
-
-struct SplitCfg {
-    static constexpr int NF = 8192, N = 4096, E = 16, T = N / E;
-    using RAD = typename Plan1D<N>::R;
-    static constexpr int BZ = 4;                          // columns per CTA in the column passes
-    static constexpr int SPAN = RowSpan<N, 4>::value;     // one column / line, padded
-    static constexpr size_t SMEM_COL = (size_t)SPAN * BZ * sizeof(float2);
-    static constexpr size_t SMEM_ROW = (size_t)SPAN * sizeof(float2);
-};
-
-// P1 for 8192-point axis-0 lines (2D).  Unit: (tile of BZ column pairs, parity r).
-template <int MAXI>
-__global__ void __launch_bounds__(SplitCfg::T * SplitCfg::BZ) p1_fwd_split(const __grid_constant__ Work<MAXI> W)
-{
-    using C = SplitCfg;
-    constexpr int E = C::E, T = C::T, BZ = C::BZ, N = C::N;
-    extern __shared__ float2 smem[];
-    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    FSP_UNIT(W, blockIdx.x, a, u);
-    const int par = u & 1, tile = u >> 1;
-    const int z0 = 2 * (tile * BZ + col);
-    const bool act = z0 < a.n2;
-    const RowView<4> sm{smem + col * C::SPAN};
-    float2 v[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int n = j + r * T;
-        float2 x = act ? __ldg(reinterpret_cast<const float2 *>(a.in[0] + gidx(a, n, 0, z0))) : make_float2(0.f, 0.f);
-        if (par) x = cmul(x, __ldg(a.tw0 + n));
-        v[r] = x;
-    }
-    line_fft<N, E, false, false, typename C::RAD>(v, j, a.twh, sm);
-#pragma unroll
-    for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
-    __syncthreads();
-    float2 *dst = a.buf0;
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int kp = j + r * T;
-        const int kx = 2 * kp + par;
-        if (kx <= N && act) {
-            const float2 q = v[r];
-            const float2 m = sm.at((N - kp - par) & (N - 1));
-            float4 o;
-            o.x = 0.5f * (q.x + m.x);
-            o.y = 0.5f * (q.y - m.y);
-            o.z = 0.5f * (q.y + m.y);
-            o.w = -0.5f * (q.x - m.x);
-            *reinterpret_cast<float4 *>(dst + iidx(a, kx, 0, z0)) = o;
-        }
-    }
-}
-
-// Adds the partner CTA's partial sums: this CTA (rank par) owns n in
-// [par * 2048, par * 2048 + 2048), i.e. registers r in [par * E/2, par * E/2 + E/2).
-template <int E, int T, class View>
-__device__ __forceinline__ void split_combine(float2 (&v)[E], int j, int par, const View &sm,
-                                             cooperative_groups::cluster_group &cluster)
-{
-#pragma unroll
-    for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
-    cluster.sync();
-#pragma unroll
-    for (int r = 0; r < E / 2; ++r) {
-        const int rr = par * (E / 2) + r;
-        const float2 *peer = cluster.map_shared_rank(&sm.at(j + rr * T), par ^ 1);
-        const float2 o = *peer;
-        v[rr] = v[rr] + o;
-    }
-    cluster.sync();
-}
-
-// P5 for 8192-point axis-0 lines (2D), 2-CTA clusters.  Unit: (tile of BZ columns, parity).
-template <int MAXI>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SplitCfg::T * SplitCfg::BZ)
-    p5_fwd_split(const __grid_constant__ Work<MAXI> W)
-{
-    using C = SplitCfg;
-    constexpr int E = C::E, T = C::T, BZ = C::BZ, N = C::N, NF = C::NF;
-    extern __shared__ float2 smem[];
-    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
-    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
-    FSP_UNIT(W, blockIdx.x, a, u);
-    const int par = (int)cluster.block_rank(), tile = u >> 1;
-    const int z = tile * BZ + col;
-    const bool act = z < a.n2;
-    const int zc = act ? z : 0;
-    const RowView<4> sm{smem + col * C::SPAN};
-    float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2];
-    for (int stream = 0; stream < 2; ++stream) {
-        if (stream == 0 && !(phi || e0)) continue;
-        if (stream == 1 && !e1) continue;
-        const float2 *src = stream == 0 ? a.buf0 : a.buf1;
-        float2 v[E];
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int k = 2 * (j + r * T) + par;
-            const int row = k <= N ? k : NF - k;
-            float2 p = src[iidx(a, row, 0, zc)];
-            if (k > N) p.y = -p.y;
-            if (stream == 0 && e0) p = (1.f + wave(k, N, a.k0s)) * p;   // W = P + i (-i k0 P)
-            v[r] = p;
-        }
-        line_fft<N, E, true, false, typename C::RAD>(v, j, a.twh, sm);
-#pragma unroll
-        for (int r = 0; r < E; ++r)
-            if (par) v[r] = cmulc(v[r], __ldg(a.tw0 + j + r * T));
-        split_combine<E, T>(v, j, par, sm, cluster);
-        if (act) {
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r) {
-                const int rr = par * (E / 2) + r;
-                const size_t g = gidx(a, j + rr * T, 0, z);
-                if (stream == 0) {
-                    if (phi) phi[g] = v[rr].x;
-                    if (e0) e0[g] = v[rr].y;
-                } else {
-                    e1[g] = v[rr].x;
-                }
-            }
-        }
-    }
-}
-
-// P3 for 8192-point contiguous lines (2D), one line per 2-CTA cluster.  Unit: (line, parity).
-template <int MAXI>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SplitCfg::T)
-    p3_fwd_split(const __grid_constant__ Work<MAXI> W, int withE)
-{
-    using C = SplitCfg;
-    constexpr int E = C::E, T = C::T, N = C::N;
-    extern __shared__ float2 smem[];
-    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
-    const int j = threadIdx.x;
-    FSP_UNIT(W, blockIdx.x, a, u);
-    const int par = (int)cluster.block_rank();
-    const int lines = (a.n0 + 1) * a.rows1;
-    const int line = u >> 1;
-    const bool act = line < lines;
-    const int lc = act ? line : 0;
-    const int n2 = a.n2;   // 4096
-    const RowView<4> sm{smem};
-    float2 *L0 = a.buf0 + (size_t)lc * n2;
-    float2 v[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int n = j + r * T;
-        float2 x = L0[n];
-        if (par) x = cmul(x, __ldg(a.tw2 + n));
-        v[r] = x;
-    }
-    line_fft<N, E, false, false, typename C::RAD>(v, j, a.twh, sm);
-    const float *Kr = krow(a, lc, 0);
-    float2 q[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int k = 2 * (j + r * T) + par;
-        const int kf = k <= n2 ? k : 2 * n2 - k;
-        v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
-        const float kk = wave(k, n2, a.k2s);
-        q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
-    }
-    line_fft<N, E, true, false, typename C::RAD>(v, j, a.twh, sm);
-#pragma unroll
-    for (int r = 0; r < E; ++r)
-        if (par) v[r] = cmulc(v[r], __ldg(a.tw2 + j + r * T));
-    split_combine<E, T>(v, j, par, sm, cluster);
-    if (act) {
-#pragma unroll
-        for (int r = 0; r < E / 2; ++r) {
-            const int rr = par * (E / 2) + r;
-            L0[j + rr * T] = v[rr];
-        }
-    }
-    if (withE) {
-        line_fft<N, E, true, false, typename C::RAD>(q, j, a.twh, sm);
-#pragma unroll
-        for (int r = 0; r < E; ++r)
-            if (par) q[r] = cmulc(q[r], __ldg(a.tw2 + j + r * T));
-        split_combine<E, T>(q, j, par, sm, cluster);
-        if (act) {
-            float2 *L1 = a.buf1 + (size_t)lc * n2;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r) {
-                const int rr = par * (E / 2) + r;
-                L1[j + rr * T] = q[rr];
-            }
         }
     }
 }
