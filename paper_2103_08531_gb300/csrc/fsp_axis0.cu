@@ -88,6 +88,14 @@ static int prep_tiles()
     return e;
 }
 
+template <int N>
+static constexpr size_t smem_p1a() { return (size_t)(2 * (N / 2) * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
+
+template <int N, int MAXI>
+struct OccA0 {
+    static inline int p1a = 1;
+};
+
 template <int N, int MAXI>
 static int prep_one()
 {
@@ -95,6 +103,10 @@ static int prep_one()
     int e = cudaFuncSetAttribute(p1_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if constexpr (N <= 512) {
         e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
+        int b = 0;
+        e |= cudaFuncSetAttribute(p1_adj_t<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1a<N>());
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p1_adj_t<N, MAXI>, TileCfg<N>::THREADS, smem_p1a<N>());
+        OccA0<N, MAXI>::p1a = std::max(1, b);
     } else {
         e |= cudaFuncSetAttribute(p1_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         e |= cudaFuncSetAttribute(p5_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
@@ -170,11 +182,21 @@ static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
         });
     }
     if (kind == PASS_P1A) {
-        return chunked(items, n, units_col<N>, [&](auto &w) {
-            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-            p1_adj<N, MAXI><<<w.offs[w.nitems], ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
-            return (int)cudaGetLastError();
-        });
+        if constexpr (N <= 512) {
+            return chunked(items, n, units_p5f<N>, [&](auto &w) {   // (y, C-column tile) units
+                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+                const int total = w.offs[w.nitems];
+                p1_adj_t<N, MAXI><<<std::min(total, sm_count() * OccA0<N, MAXI>::p1a), TileCfg<N>::THREADS,
+                                    smem_p1a<N>(), st>>>(w);
+                return (int)cudaGetLastError();
+            });
+        } else {
+            return chunked(items, n, units_col<N>, [&](auto &w) {
+                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+                p1_adj<N, MAXI><<<w.offs[w.nitems], ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
+                return (int)cudaGetLastError();
+            });
+        }
     }
     return (int)cudaErrorInvalidValue;
 }

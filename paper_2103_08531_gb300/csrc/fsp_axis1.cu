@@ -87,6 +87,14 @@ static int prep_tiles()
     return e;
 }
 
+template <int N>
+static constexpr size_t smem_p2a() { return (size_t)((N + N / 2) * TileCfg<N>::C + TileCfg<N>::EX) * sizeof(float2); }
+
+template <int N, int MAXI>
+struct OccA1 {
+    static inline int p2a = 1;
+};
+
 template <int N, int MAXI>
 static int prep_one()
 {
@@ -94,6 +102,10 @@ static int prep_one()
     int e = cudaFuncSetAttribute(p2_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if constexpr (N <= 512) {
         e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
+        int b = 0;
+        e |= cudaFuncSetAttribute(p2_adj_t<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2a<N>());
+        e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p2_adj_t<N, MAXI>, TileCfg<N>::THREADS, smem_p2a<N>());
+        OccA1<N, MAXI>::p2a = std::max(1, b);
     } else {
         e |= cudaFuncSetAttribute(p2_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         e |= cudaFuncSetAttribute(p4_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
@@ -163,6 +175,17 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
         });
     }
     if (kind == PASS_P2A) {
+        if constexpr (N <= 512) {
+            if (flag) {   // the tile version handles the three-stream adjoint (hasE)
+                return chunked(items, n, units_tile<N>, [&](auto &w) {
+                    constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+                    const int total = w.offs[w.nitems];
+                    p2_adj_t<N, MAXI><<<std::min(total, sm_count() * OccA1<N, MAXI>::p2a), TileCfg<N>::THREADS,
+                                        smem_p2a<N>(), st>>>(w);
+                    return (int)cudaGetLastError();
+                });
+            }
+        }
         return chunked(items, n, units_blk<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
             p2_adj<N, MAXI><<<w.offs[w.nitems], ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w, flag);

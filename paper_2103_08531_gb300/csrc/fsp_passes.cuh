@@ -913,6 +913,153 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_c
     cp_async_wait_all();
 }
 
+// Adjoint P1 (persistent tiles): per column z, W1 = g_phi + i g_E0 and
+// W2 = g_E1 + i g_E2 (3D) or g_E1 (2D); outputs U = F g_phi + i k0 F g_E0 ->
+// buf0 row y; F g_E1 -> buf0 row n1 + y (3D) / buf1 row y (2D); F g_E2 ->
+// buf1 row y (3D).  Unit: (y, tile of C columns).  Stage: the four inputs,
+// n0 rows x C floats each.
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_adj_t(const __grid_constant__ Work<MAXI> W)
+{
+    using C = TileCfg<N>;
+    constexpr int CC = C::C;
+    constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    float *stage = reinterpret_cast<float *>(smem);            // [4][NH][CC] floats
+    float2 *ex = smem + 2 * NH * CC;                            // after 4 * NH * CC floats
+    const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int y = u / zt, z0 = (u % zt) * CC;
+        const size_t rs = (size_t)a.n1 * a.n2 * sizeof(float);
+        for (int s = 0; s < 4; ++s)
+            if (a.in[s])
+                issue_rows<CC / 2>(reinterpret_cast<float2 *>(stage + s * NH * CC), a.in[s] + gidx(a, 0, y, z0), rs, NH,
+                                   tid, C::THREADS);
+    };
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
+    cp_async_commit();
+    ColView sm{ex + col, CC};
+    for (; w < nw; w += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int y = u / zt, z = (u % zt) * CC + col;
+        const bool has[4] = {a.in[0] != nullptr, a.in[1] != nullptr, a.in[2] != nullptr, a.in[3] != nullptr};
+        float2 v[E], q[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = make_float2(0.f, 0.f);
+            q[r] = make_float2(0.f, 0.f);
+            if (r < E / 2) {
+                const int o = (j + r * T) * CC + col;
+                v[r].x = has[0] ? stage[o] : 0.f;
+                v[r].y = has[1] ? stage[NH * CC + o] : 0.f;
+                q[r].x = has[2] ? stage[2 * NH * CC + o] : 0.f;
+                q[r].y = (has[3] && a.three_d) ? stage[3 * NH * CC + o] : 0.f;
+            }
+        }
+        __syncthreads();
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
+        cp_async_commit();
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) v[r] = q[r];
+            }
+            line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+            for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r <= E / 2; ++r) {
+                const int k = j + r * T;
+                if (k <= NH) {
+                    const float2 c = v[r];
+                    const float2 m = sm.at(k == 0 ? 0 : N - k);
+                    const float2 A = make_float2(0.5f * (c.x + m.x), 0.5f * (c.y - m.y));   // F re
+                    const float2 B = make_float2(0.5f * (c.y + m.y), -0.5f * (c.x - m.x));  // F im
+                    if (pass == 0) {
+                        const float kk = wave(k, NH, a.k0s);
+                        a.buf0[iidx(a, k, y, z)] = make_float2(A.x - kk * B.y, A.y + kk * B.x);   // A + i k0 B
+                    } else if (a.three_d) {
+                        a.buf0[iidx(a, k, a.n1 + y, z)] = A;
+                        a.buf1[iidx(a, k, y, z)] = B;
+                    } else {
+                        a.buf1[iidx(a, k, y, z)] = A;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    cp_async_wait_all();
+}
+
+// Adjoint P2 (persistent tiles): buf0 rows [0,n1) = U, [n1,2n1) = F g_E1,
+// buf1 rows [0,n1) = F g_E2 -> buf0 <- F1 U + i k1 F1(F g_E1), buf1 <- F1(F g_E2).
+// Unit: (k0, tile of C columns).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_constant__ Work<MAXI> W)
+{
+    using C = TileCfg<N>;
+    constexpr int CC = C::C;
+    constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    float2 *st0 = smem, *st1 = smem + N * CC, *ex = smem + (N + NH) * CC;
+    const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int kx = u / zt, z0 = (u % zt) * CC;
+        const size_t rs = (size_t)a.n2 * sizeof(float2);
+        issue_rows<CC>(st0, a.buf0 + iidx(a, kx, 0, z0), rs, N, tid, C::THREADS);
+        issue_rows<CC>(st1, a.buf1 + iidx(a, kx, 0, z0), rs, NH, tid, C::THREADS);
+    };
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
+    cp_async_commit();
+    ColView sm{ex + col, CC};
+    for (; w < nw; w += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / CC;
+        const int kx = u / zt, z = (u % zt) * CC + col;
+        const int n1 = a.n1;
+        float2 v[E], q[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = r < E / 2 ? st0[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
+            q[r] = r < E / 2 ? st0[(NH + j + r * T) * CC + col] : make_float2(0.f, 0.f);
+        }
+        line_fft<N, E, false, true, RAD>(v, j, a.tw1, sm);
+        line_fft<N, E, false, true, RAD>(q, j, a.tw1, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float kk = wave(j + r * T, n1, a.k1s);
+            v[r] = make_float2(v[r].x - kk * q[r].y, v[r].y + kk * q[r].x);
+            q[r] = r < E / 2 ? st1[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
+        cp_async_commit();
+#pragma unroll
+        for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
+        line_fft<N, E, false, true, RAD>(q, j, a.tw1, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = q[r];
+    }
+    cp_async_wait_all();
+}
+
 // ------------------------------------------------- warp-per-line middle pass
 
 #ifndef FSP_P3_TW
