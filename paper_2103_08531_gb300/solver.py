@@ -223,6 +223,54 @@ class Batch:
             pass
 
 
+class HostPipeline:
+    """Solves host-resident densities with copies overlapped on three streams.
+
+    Slot i of `depth` device buffer sets goes host->device on the copy-in
+    stream, is solved on the compute stream (the plan's workspace serialises
+    solves there), and returns device->host on the copy-out stream, so the
+    transfers of neighbouring solves run under each other's kernels.  Host
+    buffers should be pinned (torch.Tensor.pin_memory()) for the copies to be
+    asynchronous.
+    """
+
+    def __init__(self, plan: Plan, depth: int = 2, with_phi: bool = True, with_E: bool = True):
+        self.plan, self.depth, self.with_phi, self.with_E = plan, depth, with_phi, with_E
+        dev = plan.device
+        self.rho = [torch.empty(plan.shape, dtype=torch.float32, device=dev) for _ in range(depth)]
+        self.phi = [torch.empty(plan.shape, dtype=torch.float32, device=dev) if with_phi else None
+                    for _ in range(depth)]
+        self.E = [torch.empty((plan.dim,) + plan.shape, dtype=torch.float32, device=dev) if with_E else None
+                  for _ in range(depth)]
+        self.s_in, self.s_run, self.s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+        self.loaded = [torch.cuda.Event() for _ in range(depth)]
+        self.solved = [torch.cuda.Event() for _ in range(depth)]
+        self.freed = [torch.cuda.Event() for _ in range(depth)]
+        for e in self.freed:
+            e.record(self.s_out)
+
+    def run(self, rho_host, phi_host=None, E_host=None):
+        """rho_host: list of host tensors; phi_host / E_host: lists of host outputs (or None)."""
+        for i, r in enumerate(rho_host):
+            k = i % self.depth
+            self.s_in.wait_event(self.freed[k])
+            with torch.cuda.stream(self.s_in):
+                self.rho[k].copy_(r, non_blocking=True)
+                self.loaded[k].record(self.s_in)
+            self.s_run.wait_event(self.loaded[k])
+            self.plan.solve(self.rho[k], with_phi=self.with_phi, with_E=self.with_E, phi=self.phi[k], E=self.E[k],
+                            stream=self.s_run)
+            self.solved[k].record(self.s_run)
+            self.s_out.wait_event(self.solved[k])
+            with torch.cuda.stream(self.s_out):
+                if phi_host is not None and self.with_phi:
+                    phi_host[i].copy_(self.phi[k], non_blocking=True)
+                if E_host is not None and self.with_E:
+                    E_host[i].copy_(self.E[k], non_blocking=True)
+                self.freed[k].record(self.s_out)
+        return self.s_out
+
+
 class FspSolve(torch.autograd.Function):
     """rho -> (phi, E) with the hand-written adjoint as backward.
 

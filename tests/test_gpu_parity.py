@@ -282,6 +282,21 @@ def test_batched_rejects_repeated_plan(fsp):
         fsp.solve_batched([p, p], [r, r])
 
 
+def test_host_pipeline_matches_solve(fsp):
+    """Overlapped host->device, solve and device->host streams give the same results as plain solves."""
+    shape, h = (64, 32, 96), (0.02, 0.03, 0.01)
+    plan = fsp.Plan(shape, h, "vgf")
+    hosts = [torch.from_numpy(_mixture(shape, h, 70 + i).rho(np.float32)).pin_memory() for i in range(5)]
+    phis = [torch.empty(shape).pin_memory() for _ in hosts]
+    Es = [torch.empty((3,) + shape).pin_memory() for _ in hosts]
+    pipe = fsp.HostPipeline(plan, depth=2)
+    pipe.run(hosts, phis, Es)
+    torch.cuda.synchronize()
+    for r, ph, E in zip(hosts, phis, Es):
+        ph1, E1 = plan.solve(r.cuda())
+        assert torch.equal(ph, ph1.cpu()) and torch.equal(E, E1.cpu())
+
+
 # --------------------------------------------------------------- autotuner
 
 def _write_cache(path, arch, shape, var_tile, var_p3):
