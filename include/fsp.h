@@ -148,6 +148,16 @@ void fsp_batch_destroy(fsp_batch *batch);
 int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count);
 
 /*
+ * E = -grad(phi) by centred finite differences on the plan's grid, the
+ * alternative to Fourier differentiation that the paper compares for HE
+ * (Sec. 3, two-dimensional example): (phi[i+1] - phi[i-1]) / (2 h) inside,
+ * second-order one-sided differences on the first and last cell of each axis.
+ * phi: device float grid; E: device float [dim][grid].  Asynchronous on the
+ * stream; allocates nothing.
+ */
+int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, void *cuda_stream);
+
+/*
  * Autotuner.  Each pass has launch variants (bit 1: 8 instead of 16 values per
  * thread in column tiles; bit 2: one CTA per SM in persistent launches); the
  * choice is a process-wide table keyed by pass and padded length, read by

@@ -298,3 +298,22 @@ def adjoint_with_kernel(g2n: np.ndarray, g_phi, g_E, h) -> np.ndarray:
     _check(_load().orc_adjoint(d, _ivec(n), _dvec(h), _dp(np.ascontiguousarray(g2n)), _dp(gp), _dp(ge), _dp(out)),
            "adjoint")
     return out
+
+
+def fd_gradient(phi: np.ndarray, h) -> np.ndarray:
+    """E = -grad(phi) by centred differences, second-order one-sided at the faces.
+
+    The finite-difference field the paper sets beside Fourier differentiation
+    for HE (Sec. 3): (phi[i+1] - phi[i-1]) / (2h) inside; at i = 0 the
+    difference (-3 phi0 + 4 phi1 - phi2) / (2h) and its mirror at i = n - 1.
+    """
+    p = np.asarray(phi, dtype=np.float64)
+    out = np.empty((p.ndim,) + p.shape)
+    for a in range(p.ndim):
+        q = np.moveaxis(p, a, 0)
+        d = np.empty_like(q)
+        d[1:-1] = (q[2:] - q[:-2]) / (2 * h[a])
+        d[0] = (-3 * q[0] + 4 * q[1] - q[2]) / (2 * h[a])
+        d[-1] = (3 * q[-1] - 4 * q[-2] + q[-3]) / (2 * h[a])
+        out[a] = -np.moveaxis(d, 0, a)
+    return out

@@ -36,6 +36,7 @@ SIGNATURES = {
     "fsp_batch_destroy": (None, [_vp]),
     "fsp_plan_set_pass_events": (_i, [_vp, _vpp, _i]),
     "fsp_autotune": (_i, [_vp, ctypes.c_char_p, _i]),
+    "fsp_gradient_fd": (_i, [_vp, _vp, _vp, _vp]),
     "fsp_tuned_variant": (_i, [_i, _i]),
     "fsp_plan_kernel_spectrum": (_i, [_vp, _vp, _sz]),
     "fsp_plan_destroy": (None, [_vp]),

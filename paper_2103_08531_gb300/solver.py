@@ -121,6 +121,14 @@ class Plan:
 
     __call__ = solve
 
+    def gradient_fd(self, phi, E=None, stream=None):
+        """E = -grad(phi) by centred differences (second-order one-sided at the faces)."""
+        self._check_grid(phi, "phi")
+        if E is None:
+            E = torch.empty((self.dim,) + self.shape, dtype=torch.float32, device=phi.device)
+        _lib.check(self.lib.fsp_gradient_fd(self.handle, _ptr(phi), _ptr(E), _stream(stream)), "fsp_gradient_fd")
+        return E
+
     def adjoint(self, g_phi=None, g_E=None, g_rho=None, stream=None):
         """g_rho = A^T g_phi + sum_a B_a^T g_E[a] (either input may be None)."""
         if g_phi is None and g_E is None:

@@ -282,6 +282,17 @@ def test_batched_rejects_repeated_plan(fsp):
         fsp.solve_batched([p, p], [r, r])
 
 
+@pytest.mark.parametrize("name,shape,h", [SMALL[1], SMALL[3], ("z1024", (32, 32, 512), (0.03, 0.03, 0.004))])
+def test_fd_gradient_matches_oracle(fsp, oracle_mod, name, shape, h):
+    """Centred-difference E from the GPU phi equals the oracle's finite differences of the same phi."""
+    prob = _mixture(shape, h, seed=81)
+    plan = fsp.Plan(shape, h, "he")
+    phi, _ = plan.solve(torch.from_numpy(prob.rho(np.float32)).cuda(), with_E=False)
+    E = plan.gradient_fd(phi)
+    ref = oracle_mod.fd_gradient(phi.cpu().numpy().astype(np.float64), h)
+    assert rel(E.cpu().numpy(), ref) <= 1e-6
+
+
 def test_host_pipeline_matches_solve(fsp):
     """Overlapped host->device, solve and device->host streams give the same results as plain solves."""
     shape, h = (64, 32, 96), (0.02, 0.03, 0.01)

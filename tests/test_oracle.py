@@ -372,3 +372,30 @@ def test_he_cell_average_constants(oracle_mod):
     assert oracle_mod.he_g0_variant(3, (0.1, 0.2, 0.3), "he_nearby") == pytest.approx(1 / (4 * math.pi * 0.1))
     # cell average scales like 1/h in 3D
     assert oracle_mod.he_g0_variant(3, (0.5, 0.5, 0.5), "he_cellavg") == pytest.approx(2 * g3, rel=1e-9)
+
+
+def test_fd_gradient_exact_on_quadratics(oracle_mod):
+    """Centred and second-order one-sided differences are exact for quadratics (E = -grad phi)."""
+    shape, h = (7, 6, 5), (0.3, 0.2, 0.5)
+    x, y, z = np.meshgrid(*[np.arange(n) * hh for n, hh in zip(shape, h)], indexing="ij")
+    phi = 1.5 * x * x - 0.7 * x * y + 2.0 * z * z + 0.3 * y - z + 4.0
+    E = oracle_mod.fd_gradient(phi, h)
+    assert np.allclose(E[0], -(3.0 * x - 0.7 * y), atol=1e-12)
+    assert np.allclose(E[1], -(-0.7 * x + 0.3), atol=1e-12)
+    assert np.allclose(E[2], -(4.0 * z - 1.0), atol=1e-12)
+    # cubic terms are not exact: the scheme is second order
+    E3 = oracle_mod.fd_gradient(x ** 3, h)
+    assert np.max(np.abs(E3[0] + 3 * x ** 2)) > 1e-3
+
+
+def test_fd_gradient_second_order_for_he(oracle_mod):
+    """The paper's HE + finite-difference field converges like h^2 (Sec. 3)."""
+    errs = []
+    for n in (32, 64):
+        prob = W.unit_gaussian_2d(n, 0.05, 1.0)
+        phi, _ = oracle_mod.solve("vgf", prob.rho(np.float64), prob.h, with_E=False)
+        _, Eex = A.mixture_field(W.grid_points(prob.shape, prob.h), prob.gaussians, 2)
+        E = oracle_mod.fd_gradient(phi, prob.h)
+        inner = (slice(None), slice(2, -2), slice(2, -2))
+        errs.append(np.max(np.abs(E[inner] - Eex[inner])))
+    assert 3.0 < errs[0] / errs[1] < 5.0
