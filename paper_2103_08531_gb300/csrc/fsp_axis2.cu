@@ -64,6 +64,11 @@ int supported_axis2(int N)
     }
 }
 
+// A single forward solve takes p3_fwd1 (arguments by value) unless this is 0.
+#ifndef FSP_P3_ONE
+#define FSP_P3_ONE 1
+#endif
+
 template <int N, int MAXI>
 struct Occ2 {
     static inline int p3 = 1, p3a = 1, p3one = 1;
@@ -135,7 +140,7 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
             const int ctas = (total + C::WARPS - 1) / C::WARPS;
             // variant bit 2: one CTA per SM (else as many as fit)
             const bool one = (var & 2) != 0;
-            if (kind == PASS_P3F && MAXI == 1)
+            if (kind == PASS_P3F && MAXI == 1 && FSP_P3_ONE)
                 p3_fwd1<N><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3one)), C::THREADS, C::SMEM, st>>>(
                     w.item[0], flag);
             else if (kind == PASS_P3F)

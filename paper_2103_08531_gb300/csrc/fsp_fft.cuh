@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace fsp {
 
@@ -300,7 +301,16 @@ enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // TW_GATHER (lanes own consecutive j): passes with NS < 32 read a small table
 // laid out [r][k] after the main one (tw + N + OFF), so a warp's loads are
 // contiguous; later passes read the main table, already contiguous in k.
-enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2 };
+// TW_SMEM: as TW_GATHER, but the caller has copied the whole table (main
+// part and gathered blocks) into shared memory and passes that copy.
+enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3 };
+
+template <int TW>
+__device__ __forceinline__ float2 ldtw(const float2 *p)
+{
+    if constexpr (TW == TW_SMEM) return *p;
+    else return __ldg(p);
+}
 
 template <int SYNC>
 __device__ __forceinline__ void lsync()
@@ -313,9 +323,9 @@ __device__ __forceinline__ void lsync()
 template <int R, bool INV, int TW>
 __device__ __forceinline__ void twiddle(float2 *u, const float2 *__restrict__ tw, int m)
 {
-    if constexpr (TW == TW_TABLE || R <= 3) {
+    if constexpr (TW == TW_TABLE || TW == TW_SMEM || R <= 3) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + r * m));
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], ldtw<TW>(tw + r * m));
     } else {
         float2 w[R];
         w[1] = __ldg(tw + m);
@@ -357,6 +367,62 @@ struct NextOff {
     static constexpr int value = OFF + ((NS > 1 && NS < 32) ? R * NS : 0);
 };
 
+// Twiddles of butterfly column k (= b mod NS) in a pass with (NS, R); OFF is
+// the pass's gathered block in the TW_GATHER / TW_SMEM layouts.
+template <int N, int R, bool INV, int NS, int TW, int OFF>
+__device__ __forceinline__ void pass_twiddles(float2 *u, const float2 *__restrict__ tw, int k)
+{
+    if constexpr ((TW == TW_GATHER || TW == TW_SMEM) && NS < 32) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], ldtw<TW>(tw + N + OFF + r * NS + k));
+    } else {
+        twiddle<R, INV, TW == TW_GATHER ? TW_TABLE : TW>(u, tw, k * (N / (NS * R)));
+    }
+}
+
+// End of the gathered blocks of a radix plan (entries after the main table).
+template <int NS, int OFF, class RAD>
+struct AuxEnd;
+template <int NS, int OFF>
+struct AuxEnd<NS, OFF, Radices<>> {
+    static constexpr int value = OFF;
+};
+template <int NS, int OFF, int R, int... RS>
+struct AuxEnd<NS, OFF, Radices<R, RS...>> {
+    static constexpr int value = AuxEnd<NS * R, NextOff<NS, R, OFF>::value, Radices<RS...>>::value;
+};
+
+// Shuffle exchange before a closing radix-2 pass.  With 32 threads per line
+// (lane = j), one butterfly per thread (E = R) and NS R = N / 2, thread j's R
+// outputs sit at positions h N/2 + (j mod 16) + 16 u (h = j / 16): the next
+// pass needs positions j + 32 r, which are thread j's outputs u = h + 2 i and
+// the outputs u = (1 - h) + 2 i of lane j ^ 16.  So the exchange is a swap of
+// half the registers between lane pairs: E/2 shuffles instead of a trip
+// through shared memory.
+#ifndef FSP_SHFL_PAIR
+#define FSP_SHFL_PAIR 1
+#endif
+template <int... RS>
+struct IsClosingRadix2 : std::false_type {};
+template <>
+struct IsClosingRadix2<2> : std::true_type {};
+
+template <int E>
+__device__ __forceinline__ void pair_exchange(float2 (&v)[E], const float2 *u, int j)
+{
+    const bool hi = (j & 16) != 0;
+#pragma unroll
+    for (int i = 0; i < E / 2; ++i) {
+        const float2 keep = hi ? u[2 * i + 1] : u[2 * i];
+        const float2 send = hi ? u[2 * i] : u[2 * i + 1];
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+        v[i] = hi ? recv : keep;
+        v[E / 2 + i] = hi ? keep : recv;
+    }
+}
+
 template <int N, int E, bool INV, int NS, int R, int... RS, int SYNC, int TW, int OFF>
 struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
     template <bool PRUNE, class View>
@@ -365,7 +431,21 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
         constexpr int T = N / E;
         constexpr int Q = E / R;
         constexpr bool LAST = sizeof...(RS) == 0;
+        constexpr bool PAIR = FSP_SHFL_PAIR && SYNC == SYNC_WARP && T == 32 && Q == 1 && 2 * NS * R == N &&
+                              IsClosingRadix2<RS...>::value;
         static_assert(E % R == 0, "E must be a multiple of every radix");
+        if constexpr (PAIR) {
+            const int k = j % NS;
+            float2 u[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[r] = v[r];
+            pass_twiddles<N, R, INV, NS, TW, OFF>(u, tw, k);
+            dft<R, INV>(u);
+            pair_exchange<E>(v, u, j);
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOff<NS, R, OFF>::value>::template run<false>(v, j, tw,
+                                                                                                         sm);
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int b = j + q * T;
@@ -373,14 +453,7 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
             float2 u[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) u[r] = v[q + r * Q];
-            if constexpr (NS > 1) {
-                if constexpr (TW == TW_GATHER && NS < 32) {
-#pragma unroll
-                    for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + N + OFF + r * NS + k));
-                } else {
-                    twiddle<R, INV, TW == TW_GATHER ? TW_TABLE : TW>(u, tw, k * (N / (NS * R)));
-                }
-            }
+            if constexpr (NS > 1) pass_twiddles<N, R, INV, NS, TW, OFF>(u, tw, k);
             if constexpr (PRUNE && NS == 1) dft_half_in<R, INV>(u);
             else dft<R, INV>(u);
             if constexpr (LAST) {

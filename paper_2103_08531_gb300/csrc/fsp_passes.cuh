@@ -1063,17 +1063,11 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
 // ------------------------------------------------- warp-per-line middle pass
 
 #ifndef FSP_P3_TW
-#define FSP_P3_TW TW_POW
+#define FSP_P3_TW TW_SMEM
 #endif
 
 #ifndef FSP_P3_E32
 #define FSP_P3_E32 0
-#endif
-#ifndef FSP_P3_SAVE
-#define FSP_P3_SAVE 0
-#endif
-#ifndef FSP_P3_PREFETCH
-#define FSP_P3_PREFETCH 1
 #endif
 // Optional minimum resident blocks for the middle pass.  Leave unset: a
 // bound of 1 lets the compiler take far more registers (measured slower).
@@ -1095,8 +1089,24 @@ struct WarpCfg {
     static constexpr int PAD = 4;
     static constexpr int SPAN = RowSpan<N, PAD>::value;
     using RAD = typename P3Plan<N>::R;
-    static constexpr int SAVE = FSP_P3_SAVE;    // keep the product spectrum in shared memory, not registers
-    static constexpr size_t SMEM = (size_t)(SPAN + (SAVE ? N : 0)) * LPW * WARPS * sizeof(float2);
+    static constexpr int RL = SPAN;             // shared memory per line (exchange buffer)
+    // TW_SMEM: the twiddle table (main part and gathered blocks) after the lines
+    static constexpr int TWOFF = RL * LPW * WARPS;
+    static constexpr int TWS = FSP_P3_TW == TW_SMEM ? AuxEnd<1, N, RAD>::value : 0;
+    static constexpr size_t SMEM = (size_t)(TWOFF + TWS) * sizeof(float2);
+    // With TW_SMEM: copy the table into shared memory (every thread of the
+    // block calls this once, before its first transform) and return the copy.
+    static __device__ __forceinline__ const float2 *twiddles(float2 *smem, const float2 *gtw)
+    {
+        if constexpr (TWS > 0) {
+            float2 *stw = smem + TWOFF;
+            for (int i = threadIdx.x; i < TWS; i += THREADS) stw[i] = gtw[i];
+            __syncthreads();
+            return stw;
+        } else {
+            return gtw;
+        }
+    }
 };
 
 // Forward middle pass, one warp per line (or per 32/T lines), persistent over
@@ -1108,6 +1118,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
 {
     using C = WarpCfg<N>;
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
+    constexpr int n2 = N / 2;   // every item of a length-N launch has n2 = N / 2
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -1116,46 +1127,35 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
     // allocation of this kernel is sensitive to where the bound comes from)
     const int nw = MAXI == 1 ? ((W.item[0].n0 + 1) * W.item[0].rows1 + LPW - 1) / LPW : W.count();
     const int gstride = gridDim.x * C::WARPS;
-    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
+    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
+    const float2 *tw = C::twiddles(smem, W.item[0].tw2);   // the table depends on N only
     int g = blockIdx.x * C::WARPS + warp;
     float2 pv[E / 2];
-    if (FSP_P3_PREFETCH) {
-        const int it = W.find(g < nw ? g : 0);
+    auto fetch = [&](int gg) {
+        const int it = W.find(gg < nw ? gg : 0);
         const PassArgs &b = W.item[it];
-        const int bline = (g - W.offs[it]) * LPW + li;
-        const bool bact = g < nw && bline < (b.n0 + 1) * b.rows1;
-        const float2 *L = b.buf0 + (size_t)(bact ? bline : 0) * b.n2;
+        const int bline = (gg - W.offs[it]) * LPW + li;
+        const bool bact = gg < nw && bline < (b.n0 + 1) * b.rows1;
+        const float2 *L = b.buf0 + (size_t)(bact ? bline : 0) * n2;
 #pragma unroll
-        for (int r = 0; r < E / 2; ++r) pv[r] = bact ? L[j + r * T] : make_float2(0.f, 0.f);
-    }
+        for (int r = 0; r < E / 2; ++r)
+            if (bact) pv[r] = L[j + r * T];
+    };
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) pv[r] = make_float2(0.f, 0.f);
+    fetch(g);
     for (; g < nw; g += gstride) {
         FSP_UNIT(W, g, a, u);
-        const int n2 = a.n2;
         const int lines = (a.n0 + 1) * a.rows1;
         const int line = u * LPW + li;
         const bool act = line < lines;
         const int lc = act ? line : 0;
         float2 v[E];
-        if (!FSP_P3_PREFETCH) {
-            const float2 *L = a.buf0 + (size_t)lc * n2;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
-        }
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
-        if (FSP_P3_PREFETCH) {
-            const int ng = g + gstride;
-            const int nit = W.find(ng < nw ? ng : g);
-            const PassArgs &b = W.item[nit];
-            const int nline = (ng - W.offs[nit]) * LPW + li;
-            const bool nact = ng < nw && nline < (b.n0 + 1) * b.rows1;
-            const float2 *L = b.buf0 + (size_t)(nact ? nline : 0) * b.n2;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r)
-                if (nact) pv[r] = L[j + r * T];
-        }
+        fetch(g + gstride);
         const int kx = lc / a.rows1, row = lc % a.rows1;
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         const float *Kr = krow(a, kx, row);
         float2 q[E];
 #pragma unroll
@@ -1166,14 +1166,14 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
             const float kk = wave(k, n2, a.k2s);
             q[r] = make_float2(kk * v[r].y, -kk * v[r].x);
         }
-        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         if (act) {
             float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
         }
         if (withE) {
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(q, j, a.tw2, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(q, j, tw, sm);
             if (act) {
                 float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
@@ -1186,28 +1186,35 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
 // Single-solve forward middle pass (the arguments by value; same arithmetic
 // as p3_fwd below, kept separate because its register allocation is smaller).
 template <int N>
-__global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE)
+__global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE)
 {
     using C = WarpCfg<N>;
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
+    // the launcher runs length N on lines of n2 = N / 2 cells; a compile-time
+    // n2 turns the wavenumber and kernel-octant index arithmetic into constants
+    constexpr int n2 = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
-    const int n2 = a.n2;
     const int lines = (a.n0 + 1) * a.rows1;
     const int groups = (lines + LPW - 1) / LPW;
     const int gstride = gridDim.x * C::WARPS;
-    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
+    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
+    const float2 *tw = C::twiddles(smem, a.tw2);
     int g = blockIdx.x * C::WARPS + warp;
-    float2 pv[E / 2];
-    {
-        const int line = g * LPW + li;
-        const bool act = g < groups && line < lines;
+    float2 pv[E / 2];   // the next line's pruned input, prefetched into registers
+    auto fetch = [&](int gg) {
+        const int line = gg * LPW + li;
+        const bool act = gg < groups && line < lines;
         const float2 *L = a.buf0 + (size_t)(act ? line : 0) * n2;
 #pragma unroll
-        for (int r = 0; r < E / 2; ++r) pv[r] = act ? L[j + r * T] : make_float2(0.f, 0.f);
-    }
+        for (int r = 0; r < E / 2; ++r)
+            if (act) pv[r] = L[j + r * T];
+    };
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) pv[r] = make_float2(0.f, 0.f);
+    fetch(g);
     for (; g < groups; g += gstride) {
         const int line = g * LPW + li;
         const bool act = line < lines;
@@ -1215,17 +1222,9 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int w
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
-        {
-            const int ng = g + gstride;
-            const int nline = ng * LPW + li;
-            const bool nact = ng < groups && nline < lines;
-            const float2 *L = a.buf0 + (size_t)(nact ? nline : 0) * n2;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r)
-                if (nact) pv[r] = L[j + r * T];
-        }
+        fetch(g + gstride);
         const int kx = lc / a.rows1, row = lc % a.rows1;
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         const float *Kr = krow(a, kx, row);
         float2 u[E];
 #pragma unroll
@@ -1234,16 +1233,16 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int w
             const int kf = k <= n2 ? k : N - k;
             v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
             const float kk = wave(k, n2, a.k2s);
-            u[r] = make_float2(kk * v[r].y, -kk * v[r].x);
+            u[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
         }
-        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         if (act) {
             float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
         }
         if (withE) {
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, a.tw2, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, tw, sm);
             if (act) {
                 float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
@@ -1264,10 +1263,11 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
     const int nw = W.count();
-    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::SPAN};
+    constexpr int n2 = N / 2;   // every item of a length-N launch has n2 = N / 2
+    RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
+    const float2 *tw = C::twiddles(smem, W.item[0].tw2);   // the table depends on N only
     for (int g = blockIdx.x * C::WARPS + warp; g < nw; g += gridDim.x * C::WARPS) {
         FSP_UNIT(W, g, a, u);
-        const int n2 = a.n2;
         const int lines = (a.n0 + 1) * a.rows1;
         const int line = u * LPW + li;
         const bool act = line < lines;
@@ -1277,12 +1277,12 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = (r < E / 2 && act) ? L0[j + r * T] : make_float2(0.f, 0.f);
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         if (hasE) {
             float2 q[E];
 #pragma unroll
             for (int r = 0; r < E; ++r) q[r] = (r < E / 2 && act) ? L1[j + r * T] : make_float2(0.f, 0.f);
-            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(q, j, a.tw2, sm);
+            line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(q, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const float kk = wave(j + r * T, n2, a.k2s);
@@ -1297,7 +1297,7 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
             const int kf = k <= n2 ? k : N - k;
             v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
         }
-        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         if (act) {
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
