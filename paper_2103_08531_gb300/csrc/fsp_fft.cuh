@@ -303,12 +303,13 @@ enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // contiguous; later passes read the main table, already contiguous in k.
 // TW_SMEM: as TW_GATHER, but the caller has copied the whole table (main
 // part and gathered blocks) into shared memory and passes that copy.
-enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3 };
+// TW_STABLE: as TW_TABLE, from a copy of the main table in shared memory.
+enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4 };
 
 template <int TW>
 __device__ __forceinline__ float2 ldtw(const float2 *p)
 {
-    if constexpr (TW == TW_SMEM) return *p;
+    if constexpr (TW == TW_SMEM || TW == TW_STABLE) return *p;
     else return __ldg(p);
 }
 
@@ -323,7 +324,7 @@ __device__ __forceinline__ void lsync()
 template <int R, bool INV, int TW>
 __device__ __forceinline__ void twiddle(float2 *u, const float2 *__restrict__ tw, int m)
 {
-    if constexpr (TW == TW_TABLE || TW == TW_SMEM || R <= 3) {
+    if constexpr (TW == TW_TABLE || TW == TW_SMEM || TW == TW_STABLE || R <= 3) {
 #pragma unroll
         for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], ldtw<TW>(tw + r * m));
     } else {
@@ -402,6 +403,9 @@ struct AuxEnd<NS, OFF, Radices<R, RS...>> {
 #ifndef FSP_SHFL_PAIR
 #define FSP_SHFL_PAIR 1
 #endif
+#ifndef FSP_HALF_XCH
+#define FSP_HALF_XCH 1
+#endif
 template <int... RS>
 struct IsClosingRadix2 : std::false_type {};
 template <>
@@ -433,7 +437,47 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
         constexpr bool LAST = sizeof...(RS) == 0;
         constexpr bool PAIR = FSP_SHFL_PAIR && SYNC == SYNC_WARP && T == 32 && Q == 1 && 2 * NS * R == N &&
                               IsClosingRadix2<RS...>::value;
+        // Block-synchronous form of the same lane-pair swap: only the half of
+        // the outputs that changes thread goes through shared memory.  The
+        // branches are warp-uniform in column tiles (j = tid / columns).
+        constexpr bool HALF = FSP_HALF_XCH && SYNC == SYNC_BLOCK && T == 32 && Q == 1 && 2 * NS * R == N &&
+                              IsClosingRadix2<RS...>::value;
         static_assert(E % R == 0, "E must be a multiple of every radix");
+        if constexpr (HALF) {
+            const int k = j % NS;
+            float2 u[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[r] = v[r];
+            pass_twiddles<N, R, INV, NS, TW, OFF>(u, tw, k);
+            dft<R, INV>(u);
+            const bool hi = (j & 16) != 0;
+            // output u of thread j sits at position hi N/2 + (j mod 16) + 16 u
+            if (hi) {
+#pragma unroll
+                for (int i = 0; i < E / 2; ++i) sm.at(N / 2 + (j & 15) + 32 * i) = u[2 * i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < E / 2; ++i) sm.at(j + 16 + 32 * i) = u[2 * i + 1];
+            }
+            lsync<SYNC>();
+            if (hi) {
+#pragma unroll
+                for (int i = 0; i < E / 2; ++i) {
+                    v[i] = sm.at(j + 32 * i);
+                    v[E / 2 + i] = u[2 * i + 1];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < E / 2; ++i) {
+                    v[i] = u[2 * i];
+                    v[E / 2 + i] = sm.at(j + 32 * (E / 2 + i));
+                }
+            }
+            lsync<SYNC>();
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOff<NS, R, OFF>::value>::template run<false>(v, j, tw,
+                                                                                                         sm);
+            return;
+        }
         if constexpr (PAIR) {
             const int k = j % NS;
             float2 u[R];

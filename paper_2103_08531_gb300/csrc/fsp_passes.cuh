@@ -645,6 +645,12 @@ struct TilePlan<N, 8> {
     using R = typename Plan1D<N>::R;
 };
 
+// Twiddle source of the column tiles: a copy of the table in shared memory
+// (TW_STABLE) or the global table through the read-only cache (TW_TABLE).
+#ifndef FSP_TILE_TW
+#define FSP_TILE_TW TW_STABLE
+#endif
+
 // EE = 16: 16 values per thread (Plan16); EE = 8: Plan1D (8 per thread, 12 for 192).
 template <int N, int EE = 16>
 struct TileCfg {
@@ -653,8 +659,30 @@ struct TileCfg {
     static constexpr int C = FSP_TILE_C;           // columns per tile (complex)
     static constexpr int THREADS = T * C;
     using RAD = typename TilePlan<N, EE>::R;
-    static constexpr int EX = N * C;                // exchange buffer, float2
+    static constexpr int TWS = FSP_TILE_TW == TW_STABLE ? N : 0;
+    // exchange buffer (N x C), then the twiddle copy; the last region of
+    // every tile kernel's shared memory, in float2
+    static constexpr int EX = N * C + TWS;
+    // Every thread calls this once, before its first transform.
+    static __device__ __forceinline__ const float2 *twiddles(float2 *ex, const float2 *gtw)
+    {
+        if constexpr (TWS > 0) {
+            float2 *stw = ex + N * C;
+            for (int i = threadIdx.x; i < TWS; i += THREADS) stw[i] = gtw[i];
+            __syncthreads();
+            return stw;
+        } else {
+            return gtw;
+        }
+    }
 };
+
+// Column-tile transform: block-synchronous, twiddles from FSP_TILE_TW.
+template <int N, int E, bool INV, bool PRUNE_IN, class RAD>
+__device__ __forceinline__ void tile_fft(float2 (&v)[E], int j, const float2 *__restrict__ tw, const ColView &sm)
+{
+    line_fft<N, E, INV, PRUNE_IN, RAD, ColView, SYNC_BLOCK, FSP_TILE_TW>(v, j, tw, sm);
+}
 
 // Rows [0, nrows) of C complex (8 C bytes) each into dst (row r at dst + C r).
 template <int C>
@@ -692,6 +720,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p1_fwd(const __grid_c
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
+    const float2 *tw = C::twiddles(ex, W.item[0].tw0);   // the table depends on N only
     for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
@@ -705,7 +734,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p1_fwd(const __grid_c
         __syncthreads();
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
-        line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+        tile_fft<N, E, false, true, RAD>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
         __syncthreads();
@@ -749,6 +778,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p2_fwd(const __grid_c
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
+    const float2 *tw = C::twiddles(ex, W.item[0].tw1);   // the table depends on N only
     for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
@@ -761,7 +791,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p2_fwd(const __grid_c
         __syncthreads();
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
-        line_fft<N, E, false, true, RAD>(v, j, a.tw1, sm);
+        tile_fft<N, E, false, true, RAD>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
     }
@@ -793,6 +823,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p4_fwd(const __grid_c
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
+    const float2 *tw = C::twiddles(ex, W.item[0].tw1);   // the table depends on N only
     for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
@@ -810,7 +841,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p4_fwd(const __grid_c
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
         if (withE) {
-            line_fft<N, E, true, false, RAD>(q, j, a.tw1, sm);
+            tile_fft<N, E, true, false, RAD>(q, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = q[r];
 #pragma unroll
@@ -818,11 +849,11 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p4_fwd(const __grid_c
                 const float kk = wave(j + r * T, n1, a.k1s);
                 q[r] = make_float2(kk * v[r].y, -kk * v[r].x);
             }
-            line_fft<N, E, true, false, RAD>(q, j, a.tw1, sm);
+            tile_fft<N, E, true, false, RAD>(q, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = q[r];
         }
-        line_fft<N, E, true, false, RAD>(v, j, a.tw1, sm);
+        tile_fft<N, E, true, false, RAD>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
     }
@@ -860,6 +891,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_c
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
+    const float2 *tw = C::twiddles(ex, W.item[0].tw0);   // the table depends on N only
     for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
@@ -892,7 +924,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_c
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
         if (first) {
-            line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
+            tile_fft<N, E, true, false, RAD>(v, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) {
                 const size_t g = gidx(a, j + r * T, y, z);
@@ -901,7 +933,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_c
             }
         }
         if (second) {
-            line_fft<N, E, true, false, RAD>(q, j, a.tw0, sm);
+            tile_fft<N, E, true, false, RAD>(q, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) {
                 const size_t g = gidx(a, j + r * T, y, z);
@@ -944,6 +976,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_adj_t(const __grid_con
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
+    const float2 *tw = C::twiddles(ex, W.item[0].tw0);   // the table depends on N only
     for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
@@ -972,7 +1005,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_adj_t(const __grid_con
 #pragma unroll
                 for (int r = 0; r < E; ++r) v[r] = q[r];
             }
-            line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+            tile_fft<N, E, false, true, RAD>(v, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
             __syncthreads();
@@ -1027,6 +1060,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
+    const float2 *tw = C::twiddles(ex, W.item[0].tw1);   // the table depends on N only
     for (; w < nw; w += gridDim.x) {
         cp_async_wait_all();
         __syncthreads();
@@ -1040,8 +1074,8 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
             v[r] = r < E / 2 ? st0[(j + r * T) * CC + col] : make_float2(0.f, 0.f);
             q[r] = r < E / 2 ? st0[(NH + j + r * T) * CC + col] : make_float2(0.f, 0.f);
         }
-        line_fft<N, E, false, true, RAD>(v, j, a.tw1, sm);
-        line_fft<N, E, false, true, RAD>(q, j, a.tw1, sm);
+        tile_fft<N, E, false, true, RAD>(v, j, tw, sm);
+        tile_fft<N, E, false, true, RAD>(q, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const float kk = wave(j + r * T, n1, a.k1s);
@@ -1053,7 +1087,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
         cp_async_commit();
 #pragma unroll
         for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
-        line_fft<N, E, false, true, RAD>(q, j, a.tw1, sm);
+        tile_fft<N, E, false, true, RAD>(q, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = q[r];
     }
