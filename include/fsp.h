@@ -20,8 +20,9 @@
  * Units follow the paper: G = 1/(4 pi r) in 3D and -ln(r)/(2 pi) in 2D.
  *
  * Layouts.  All arrays are row-major with the last axis contiguous:
- *   3D rho, phi: float [nx][ny][nz];   E: float [3][nx][ny][nz]
- *   2D rho, phi: float [nx][ny];       E: float [2][nx][ny]
+ *   3D rho, phi: real [nx][ny][nz];   E: real [3][nx][ny][nz]
+ *   2D rho, phi: real [nx][ny];       E: real [2][nx][ny]
+ * "real" is float for FSP_F32 plans and double for FSP_F64 plans.
  * Device pointers must be 16-byte aligned; the caller owns every buffer.
  *
  * Execution.  Solves are asynchronous on the given CUDA stream (a
@@ -72,21 +73,34 @@ enum fsp_status {
  * (paper Sec. 2, last paragraph: transform of G^L on an oversampled grid,
  * restricted to the 2N grid) and stores the real, even FP32 spectrum of the
  * kernel with prod(h)/prod(2n) folded in.  Blocks until the precomputation
- * has finished.  Supported sizes: 3D, 2 n_a in {64, 128, 192, 256, 512, 1024}
- * on every axis; 2D, 2 n_a in {64, 128, 192, 256, 512, 1024, 2048, 4096,
- * 8192}; the contiguous axis has an even n.  Others: FSP_ERR_UNSUPPORTED_SIZE.
- * dtype: FSP_F32 only (FSP_F64 returns FSP_ERR_UNSUPPORTED_SIZE).
+ * has finished.
+ *
+ * Two solve paths.  The FFT passes (FP32) cover: 3D, 2 n_a in {64, 128, 192,
+ * 256, 512, 1024} on every axis; 2D, 2 n_a in {64, 128, 192, 256, 512, 1024,
+ * 2048, 4096, 8192}; the contiguous axis with an even n.  Every other size
+ * with 1 <= n_a <= 512, and every FSP_F64 plan, runs the direct-sum path: the
+ * same pruned convolution with each 1D transform taken by its definition
+ * (O(N^2) per line), in the plan's precision -- the paper's convergence
+ * studies use N = 10 ... 100 per axis (Sec. 3), 2 N often with large prime
+ * factors.  Larger odd-size grids: FSP_ERR_UNSUPPORTED_SIZE.
+ * dtype: FSP_F32 (float buffers) or FSP_F64 (double buffers everywhere a
+ * solve, adjoint or gradient takes a grid).
  * Returns NULL on failure (see fsp_last_error()).
  */
 fsp_plan *fsp_plan_create(int nx, int ny, int nz, double hx, double hy, double hz, int method, int dtype);
 
+enum fsp_plan_flags {
+    FSP_PLAN_DIRECT = 1   /* run the direct-sum path even where the FFT passes cover the size */
+};
+
 /*
  * As fsp_plan_create, with the VGF truncation radius scaled by lambda (L =
- * lambda * box diagonal; lambda <= 0 means 1) and, for the HE methods, an
- * explicit value g0 for G(0) (NaN means the method's default).
+ * lambda * box diagonal; lambda <= 0 means 1), for the HE methods an explicit
+ * value g0 for G(0) (NaN means the method's default), and flags (a set of
+ * fsp_plan_flags; unknown bits: FSP_ERR_INVALID).
  */
 fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, double hy, double hz, int method, int dtype,
-                             double lambda, double g0);
+                             double lambda, double g0, int flags);
 
 int fsp_last_error(void);
 const char *fsp_error_string(int status);
@@ -105,8 +119,8 @@ size_t fsp_plan_workspace_bytes(const fsp_plan *plan, int with_E, int batch);
 int fsp_plan_set_workspace(fsp_plan *plan, void *dev_ptr, size_t bytes);
 
 /*
- * One solve.  rho: device float grid.  phi: device float grid or NULL.
- * E: device float [dim][grid] or NULL.  phi and E must not both be NULL.
+ * One solve.  rho: device real grid.  phi: device real grid or NULL.
+ * E: device real [dim][grid] or NULL.  phi and E must not both be NULL.
  */
 int fsp_solve(fsp_plan *plan, const void *rho, void *phi, void *E, void *cuda_stream);
 
@@ -122,7 +136,8 @@ int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *g_E, void *
  * Many independent solves of different geometries, one launch per pass over
  * all of them.  plans[i] must be distinct plans, each with its own workspace
  * set; rho/phi/E as for fsp_solve (phi[i] or E[i] may be NULL consistently for
- * all i: with_E is taken from E != NULL).
+ * all i: with_E is taken from E != NULL).  Direct-path plans (see
+ * fsp_plan_create) are solved one after another after the batched launches.
  */
 int fsp_solve_batched(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
                       void *const *E, void *cuda_stream);
@@ -152,7 +167,7 @@ int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count);
  * alternative to Fourier differentiation that the paper compares for HE
  * (Sec. 3, two-dimensional example): (phi[i+1] - phi[i-1]) / (2 h) inside,
  * second-order one-sided differences on the first and last cell of each axis.
- * phi: device float grid; E: device float [dim][grid].  Asynchronous on the
+ * phi: device real grid; E: device real [dim][grid].  Asynchronous on the
  * stream; allocates nothing.
  */
 int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, void *cuda_stream);
@@ -167,7 +182,8 @@ int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, void *cuda_s
  * of them.  With a cache_path the table is written back, keyed by GPU
  * architecture.  This call allocates scratch buffers and synchronises (it is
  * set-up, not a solve).  fsp_tuned_variant reports an entry: kind is 0..7 for
- * p1_fwd, p1_adj, p2_fwd, p2_adj, p3_fwd, p3_adj, p4_fwd, p5_fwd.
+ * p1_fwd, p1_adj, p2_fwd, p2_adj, p3_fwd, p3_adj, p4_fwd, p5_fwd.  Direct-path
+ * plans have nothing to tune (mode 0 behaviour).
  */
 int fsp_autotune(fsp_plan *plan, const char *cache_path, int mode);
 int fsp_tuned_variant(int kind, int N);

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libfsp.so")
 
 FSP_HE, FSP_VGF, FSP_HE_NEARBY, FSP_HE_CELLAVG = 0, 1, 2, 3
 FSP_F32, FSP_F64 = 0, 1
+FSP_PLAN_DIRECT = 1
 STATUS = {0: "FSP_OK", 1: "FSP_ERR_INVALID", 2: "FSP_ERR_UNSUPPORTED_SIZE", 3: "FSP_ERR_CUDA",
           4: "FSP_ERR_NOMEM", 5: "FSP_ERR_WORKSPACE", 6: "FSP_ERR_TIMEOUT"}
 
@@ -22,7 +23,7 @@ _vp, _i, _d, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size
 _ip, _dp, _vpp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)
 SIGNATURES = {
     "fsp_plan_create": (_vp, [_i, _i, _i, _d, _d, _d, _i, _i]),
-    "fsp_plan_create_ex": (_vp, [_i, _i, _i, _d, _d, _d, _i, _i, _d, _d]),
+    "fsp_plan_create_ex": (_vp, [_i, _i, _i, _d, _d, _d, _i, _i, _d, _d, _i]),
     "fsp_last_error": (_i, []),
     "fsp_error_string": (ctypes.c_char_p, [_i]),
     "fsp_plan_geometry": (_i, [_vp, _ip, _ip, _dp, _dp, _ip]),

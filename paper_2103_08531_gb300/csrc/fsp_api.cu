@@ -97,19 +97,17 @@ static void plan_free(Plan &p)
     if (p.tw1 != p.tw0) cudaFree(p.tw1);
     if (p.tw2 != p.tw0 && p.tw2 != p.tw1) cudaFree(p.tw2);
     cudaFree(p.K);
+    cudaFree(p.K64);
+    for (int a = 0; a < 3; ++a) cudaFree(p.dtw[a]);
 }
 
 extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, double hy, double hz, int method,
-                                        int dtype, double lambda, double g0)
+                                        int dtype, double lambda, double g0, int flags)
 {
     const int dim = nz == 0 ? 2 : 3;
     if (nx <= 0 || ny <= 0 || nz < 0 || !(hx > 0) || !(hy > 0) || (dim == 3 && !(hz > 0)) || method < FSP_HE ||
-        method > FSP_HE_CELLAVG) {
+        method > FSP_HE_CELLAVG || (dtype != FSP_F32 && dtype != FSP_F64) || (flags & ~FSP_PLAN_DIRECT)) {
         set_err(FSP_ERR_INVALID);
-        return nullptr;
-    }
-    if (dtype != FSP_F32) {
-        set_err(dtype == FSP_F64 ? FSP_ERR_UNSUPPORTED_SIZE : FSP_ERR_INVALID);
         return nullptr;
     }
     fsp_plan *handle = new (std::nothrow) fsp_plan();
@@ -137,9 +135,14 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     p.k0s = (float)(2.0 * pi / (2.0 * p.n0 * hh0));
     p.k1s = dim == 3 ? (float)(2.0 * pi / (2.0 * ny * hy)) : 0.f;
     p.k2s = (float)(2.0 * pi / (2.0 * p.n2 * hh2));
-    bool ok = supported_axis0(2 * p.n0) && supported_axis2(2 * p.n2) && (p.n2 % 2 == 0) &&
-              (dim == 2 || (supported_axis1(2 * p.n1) && 2 * p.n0 <= 1024 && 2 * p.n2 <= 1024));
-    if (!ok) {
+    p.kd[0] = 2.0 * pi / (2.0 * p.n0 * hh0);
+    p.kd[1] = dim == 3 ? 2.0 * pi / (2.0 * ny * hy) : 0.0;
+    p.kd[2] = 2.0 * pi / (2.0 * p.n2 * hh2);
+    p.dtype = dtype;
+    const bool fast = supported_axis0(2 * p.n0) && supported_axis2(2 * p.n2) && (p.n2 % 2 == 0) &&
+                      (dim == 2 || (supported_axis1(2 * p.n1) && 2 * p.n0 <= 1024 && 2 * p.n2 <= 1024));
+    p.direct = dtype == FSP_F64 || (flags & FSP_PLAN_DIRECT) || !fast;
+    if (p.direct && (p.n0 > DIRECT_MAX_N || p.n2 > DIRECT_MAX_N || (dim == 3 && p.n1 > DIRECT_MAX_N))) {
         delete handle;
         set_err(FSP_ERR_UNSUPPORTED_SIZE);
         return nullptr;
@@ -157,7 +160,7 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
         set_err(FSP_ERR_CUDA);
         return nullptr;
     }
-    {
+    if (!p.direct) {
         std::lock_guard<std::mutex> lk(g_prep_mutex);
         int e = prepare_axis0(2 * p.n0) | prepare_axis2(2 * p.n2) | (dim == 3 ? prepare_axis1(2 * p.n1) : 0);
         if (e) {
@@ -168,24 +171,35 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     }
     int rc = FSP_OK;
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
-    if (cudaMalloc(&p.tw0, sizeof(float2) * (N0 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
-    if (rc == FSP_OK) {
+    if (p.direct) {
+        const int Ns[3] = {N0, dim == 3 ? N1 : 0, N2};
+        for (int a = 0; a < 3 && rc == FSP_OK; ++a)
+            if (Ns[a] && cudaMalloc(&p.dtw[a], sizeof(double2) * Ns[a]) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    } else if (cudaMalloc(&p.tw0, sizeof(float2) * (N0 + TW_AUX)) != cudaSuccess) {
+        rc = FSP_ERR_NOMEM;
+    }
+    if (rc == FSP_OK && !p.direct) {
         if (dim == 3 && N1 != N0) {
             if (cudaMalloc(&p.tw1, sizeof(float2) * (N1 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
         } else {
             p.tw1 = p.tw0;
         }
     }
-    if (rc == FSP_OK) {
+    if (rc == FSP_OK && !p.direct) {
         if (N2 == N0) p.tw2 = p.tw0;
         else if (dim == 3 && N2 == N1) p.tw2 = p.tw1;
         else if (cudaMalloc(&p.tw2, sizeof(float2) * (N2 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
     }
     p.K_count = (size_t)(p.n[0] + 1) * (p.n[1] + 1) * (dim == 3 ? (p.n[2] + 1) : 1);
     if (rc == FSP_OK && cudaMalloc(&p.K, sizeof(float) * p.K_count) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    if (rc == FSP_OK && dtype == FSP_F64 && cudaMalloc(&p.K64, sizeof(double) * p.K_count) != cudaSuccess)
+        rc = FSP_ERR_NOMEM;
     cudaStream_t st = nullptr;
     if (rc == FSP_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = FSP_ERR_CUDA;
-    if (rc == FSP_OK) {
+    if (rc == FSP_OK && p.direct) {
+        for (int a = 0; a < 3 && rc == FSP_OK; ++a)
+            if (p.dtw[a] && make_direct_twiddles(p.dtw[a], a == 0 ? N0 : a == 1 ? N1 : N2, st)) rc = FSP_ERR_CUDA;
+    } else if (rc == FSP_OK) {
         if (make_twiddles(p.tw0, N0, st) || make_twiddles_aux(p.tw0, N0, st)) rc = FSP_ERR_CUDA;
         if (rc == FSP_OK && p.tw1 != p.tw0 && (make_twiddles(p.tw1, N1, st) || make_twiddles_aux(p.tw1, N1, st)))
             rc = FSP_ERR_CUDA;
@@ -208,7 +222,7 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
 
 extern "C" fsp_plan *fsp_plan_create(int nx, int ny, int nz, double hx, double hy, double hz, int method, int dtype)
 {
-    return fsp_plan_create_ex(nx, ny, nz, hx, hy, hz, method, dtype, 1.0, NAN);
+    return fsp_plan_create_ex(nx, ny, nz, hx, hy, hz, method, dtype, 1.0, NAN, 0);
 }
 
 extern "C" void fsp_plan_destroy(fsp_plan *plan)
@@ -234,7 +248,10 @@ extern "C" int fsp_plan_geometry(const fsp_plan *plan, int *dim, int *n, double 
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static size_t per_solve_bytes(const Plan &p) { return 2 * align_up(p.buf_elems * sizeof(float2), 256); }
+static size_t per_solve_bytes(const Plan &p)
+{
+    return p.direct ? direct_workspace_bytes(p) : 2 * align_up(p.buf_elems * sizeof(float2), 256);
+}
 
 extern "C" size_t fsp_plan_workspace_bytes(const fsp_plan *plan, int with_E, int batch)
 {
@@ -330,6 +347,7 @@ static PassArgs fwd_args(const Plan &p, void *ws, const float *rho, float *phi, 
 // Forward pipeline for one plan on its workspace `ws`.
 int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
 {
+    if (p.direct) return run_direct_forward(p, ws, rho, phi, E, st);   // buffers in the plan's precision
     PassArgs a = fwd_args(p, ws, rho, phi, E);
     const int withE = E != nullptr;
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
@@ -354,6 +372,7 @@ int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E,
 
 int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, float *g_rho, cudaStream_t st)
 {
+    if (p.direct) return run_direct_adjoint(p, ws, g_phi, g_E, g_rho, st);
     if (!g_E) return run_forward(p, ws, g_phi, g_rho, nullptr, st);   // A is symmetric
     PassArgs a = base_args(p, ws);
     const size_t c = cells(p);
@@ -464,8 +483,16 @@ extern "C" int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *
 
 // ----------------------------------------------------------------- batches
 
+// Direct-path items of a batch run one after another after the fast launches.
+struct DirectJob {
+    const Plan *p;
+    const void *rho;
+    void *phi, *E;
+};
+
 struct fsp_batch {
     std::vector<PassLaunch> launches;
+    std::vector<DirectJob> direct;
 };
 
 static int check_batch(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi, void *const *E)
@@ -484,18 +511,32 @@ static int check_batch(fsp_plan *const *plans, int count, const void *const *rho
     return FSP_OK;
 }
 
-static std::vector<PassLaunch> plan_batch(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
-                                          void *const *E)
+static void plan_batch(fsp_batch &b, fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
+                       void *const *E)
 {
     std::vector<const Plan *> ps;
     std::vector<PassArgs> items;
     for (int i = 0; i < count; ++i) {
         const Plan &p = plans[i]->p;
+        if (p.direct) {
+            b.direct.push_back({&p, rho[i], phi ? phi[i] : nullptr, E ? E[i] : nullptr});
+            continue;
+        }
         ps.push_back(&p);
         items.push_back(fwd_args(p, p.ws, (const float *)rho[i], phi ? (float *)phi[i] : nullptr,
                                  E ? (float *)E[i] : nullptr));
     }
-    return batch_launches(ps, items, E != nullptr);
+    if (!items.empty()) b.launches = batch_launches(ps, items, E != nullptr);
+}
+
+static int run_batch(const fsp_batch &b, cudaStream_t st)
+{
+    int rc = run_launches(b.launches, st);
+    for (size_t i = 0; i < b.direct.size() && rc == FSP_OK; ++i) {
+        const DirectJob &d = b.direct[i];
+        rc = run_direct_forward(*d.p, d.p->ws, d.rho, d.phi, d.E, st);
+    }
+    return rc;
 }
 
 extern "C" int fsp_solve_batched(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
@@ -503,7 +544,9 @@ extern "C" int fsp_solve_batched(fsp_plan *const *plans, int count, const void *
 {
     int rc = check_batch(plans, count, rho, phi, E);
     if (rc) return set_err(rc);
-    return set_err(run_launches(plan_batch(plans, count, rho, phi, E), (cudaStream_t)cuda_stream));
+    fsp_batch b;
+    plan_batch(b, plans, count, rho, phi, E);
+    return set_err(run_batch(b, (cudaStream_t)cuda_stream));
 }
 
 extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
@@ -519,7 +562,7 @@ extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const 
         set_err(FSP_ERR_NOMEM);
         return nullptr;
     }
-    b->launches = plan_batch(plans, count, rho, phi, E);
+    plan_batch(*b, plans, count, rho, phi, E);
     set_err(FSP_OK);
     return b;
 }
@@ -527,7 +570,7 @@ extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const 
 extern "C" int fsp_batch_solve(fsp_batch *b, void *cuda_stream)
 {
     if (!b) return set_err(FSP_ERR_INVALID);
-    return set_err(run_launches(b->launches, (cudaStream_t)cuda_stream));
+    return set_err(run_batch(*b, (cudaStream_t)cuda_stream));
 }
 
 extern "C" void fsp_batch_destroy(fsp_batch *b) { delete b; }

@@ -142,7 +142,7 @@ extern "C" int fsp_autotune(fsp_plan *plan, const char *cache_path, int mode)
                 if (!have_cache[k][i]) g_var[k][i] = before[k][i];
             }
     }
-    if (mode == 0) return FSP_OK;
+    if (mode == 0 || p.direct) return FSP_OK;
 
     struct Job {
         int kind, N, slot;   // slot: index of the pass in the forward pipeline (event interval)

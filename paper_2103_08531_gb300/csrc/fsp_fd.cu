@@ -10,16 +10,18 @@
 
 namespace {
 
-__device__ __forceinline__ float deriv(const float *__restrict__ phi, size_t c, int i, int n, size_t stride, float inv2h)
+template <class R>
+__device__ __forceinline__ R deriv(const R *__restrict__ phi, size_t c, int i, int n, size_t stride, R inv2h)
 {
-    if (n < 3) return 0.f;
-    if (i == 0) return (-3.f * phi[c] + 4.f * phi[c + stride] - phi[c + 2 * stride]) * inv2h;
-    if (i == n - 1) return (3.f * phi[c] - 4.f * phi[c - stride] + phi[c - 2 * stride]) * inv2h;
+    if (n < 3) return R(0);
+    if (i == 0) return (R(-3) * phi[c] + R(4) * phi[c + stride] - phi[c + 2 * stride]) * inv2h;
+    if (i == n - 1) return (R(3) * phi[c] - R(4) * phi[c - stride] + phi[c - 2 * stride]) * inv2h;
     return (phi[c + stride] - phi[c - stride]) * inv2h;
 }
 
-__global__ void k_fd_gradient(const float *__restrict__ phi, float *__restrict__ E, int n0, int n1, int n2, int dim,
-                              float i0, float i1, float i2)
+template <class R>
+__global__ void k_fd_gradient(const R *__restrict__ phi, R *__restrict__ E, int n0, int n1, int n2, int dim, R i0,
+                              R i1, R i2)
 {
     const size_t cells = (size_t)n0 * n1 * n2;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < cells; c += (size_t)gridDim.x * blockDim.x) {
@@ -43,13 +45,18 @@ extern "C" int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, v
     if (!plan || !phi || !E) return FSP_ERR_INVALID;
     if (((uintptr_t)phi % 16) || ((uintptr_t)E % 16)) return FSP_ERR_INVALID;
     const fsp::Plan &p = plan->p;
-    const float i0 = (float)(0.5 / p.h[0]);
-    const float i1 = p.dim == 3 ? (float)(0.5 / p.h[1]) : 0.f;
-    const float i2 = (float)(0.5 / (p.dim == 3 ? p.h[2] : p.h[1]));
+    const double i0 = 0.5 / p.h[0];
+    const double i1 = p.dim == 3 ? 0.5 / p.h[1] : 0.0;
+    const double i2 = 0.5 / (p.dim == 3 ? p.h[2] : p.h[1]);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_fd_gradient<<<sms * 8, 256, 0, (cudaStream_t)cuda_stream>>>((const float *)phi, (float *)E, p.n0, p.n1, p.n2,
-                                                                   p.dim, i0, i1, i2);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (p.dtype == FSP_F64)
+        k_fd_gradient<double><<<sms * 8, 256, 0, st>>>((const double *)phi, (double *)E, p.n0, p.n1, p.n2, p.dim, i0,
+                                                       i1, i2);
+    else
+        k_fd_gradient<float><<<sms * 8, 256, 0, st>>>((const float *)phi, (float *)E, p.n0, p.n1, p.n2, p.dim,
+                                                      (float)i0, (float)i1, (float)i2);
     return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ERR_CUDA;
 }

@@ -32,6 +32,12 @@ struct Plan {
     int device;
     cudaEvent_t pass_ev[8];   // optional per-pass timing events (see fsp_plan_set_pass_events)
     int n_pass_ev;
+    // direct-sum path (fsp_direct.cu): sizes the fast passes do not cover, and FP64
+    int dtype;                // FSP_F32 or FSP_F64
+    int direct;               // 1: solves run the direct-sum DFT path
+    double *K64;              // FP64 kernel octant (FP64 plans)
+    double2 *dtw[3];          // FP64 twiddles exp(2 pi i m / (2 n_a)) per pass axis (direct plans)
+    double kd[3];             // 2 pi / (2 n_a h_a) per pass axis, FP64
 };
 
 // fsp_precompute.cu
@@ -57,6 +63,13 @@ int prepare_axis2(int N);
 int launch_axis0(int kind, int N, const PassArgs *items, int n, int var, cudaStream_t st);
 int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
 int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
+
+// fsp_direct.cu: the direct-sum DFT path (any size, FP32 or FP64)
+constexpr int DIRECT_MAX_N = 512;   // cells per axis
+size_t direct_workspace_bytes(const Plan &p);
+int run_direct_forward(const Plan &p, void *ws, const void *rho, void *phi, void *E, cudaStream_t st);
+int run_direct_adjoint(const Plan &p, void *ws, const void *g_phi, const void *g_E, void *g_rho, cudaStream_t st);
+int make_direct_twiddles(double2 *tw, int N, cudaStream_t st);   // fsp_precompute.cu
 
 // fsp_autotune.cu: the variant chosen for a pass kind at padded length N (0 if untuned)
 int tuned_variant(int kind, int N);

@@ -43,6 +43,22 @@ int make_twiddles(float2 *tw, int N, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// FP64 table for the direct-sum path: (cos, sin) of 2 pi m / N.
+__global__ void k_direct_twiddles(double2 *tw, int N)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)N, &s, &c);
+    tw[m] = make_double2(c, s);
+}
+
+int make_direct_twiddles(double2 *tw, int N, cudaStream_t st)
+{
+    k_direct_twiddles<<<(N + 255) / 256, 256, 0, st>>>(tw, N);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // ---------------------------------------------------------- axis matrices
 
 // cos(pi a / b) for integers, argument reduced exactly first.
@@ -236,9 +252,16 @@ __global__ void k_scale_to_f32(const double *src, float *dst, size_t n, double s
         dst[i] = (float)(src[i] * s);
 }
 
+__global__ void k_scale_f64(const double *src, double *dst, size_t n, double s)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] * s;
+}
+
 // ------------------------------------------------------------------ driver
 
-// Builds the FP32 octant K into plan->K (device).  Returns an fsp_status.
+// Builds the FP32 octant K into plan->K (device), and the FP64 one into
+// plan->K64 when that is allocated.  Returns an fsp_status.
 int build_kernel_spectrum(Plan *p, cudaStream_t st)
 {
     const int d = p->dim;
@@ -308,6 +331,7 @@ int build_kernel_spectrum(Plan *p, cudaStream_t st)
             size_t oct = 1;
             for (int a = 0; a < d; ++a) oct *= (size_t)(n[a] + 1);
             k_scale_to_f32<<<1024, 256, 0, st>>>(src, p->K, oct, scale);
+            if (p->K64) k_scale_f64<<<1024, 256, 0, st>>>(src, p->K64, oct, scale);
         }
     }
     if (rc == FSP_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FSP_ERR_CUDA;

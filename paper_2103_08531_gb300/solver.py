@@ -27,28 +27,39 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+DTYPES = {"f32": (_lib.FSP_F32, torch.float32), "f64": (_lib.FSP_F64, torch.float64)}
+
+
 class Plan:
     """One grid geometry: shape (nx, ny[, nz]) cells of spacing h, method 'vgf' or 'he'.
 
     Creating it runs the FP64 kernel precomputation on the current CUDA device
-    and allocates the plan's workspace with torch.
+    and allocates the plan's workspace with torch.  dtype 'f32' or 'f64' sets
+    the precision of the grids the plan takes and returns; direct=True runs
+    the direct-sum path even where the FFT passes cover the size (sizes they
+    do not cover, and every 'f64' plan, run it anyway).
     """
 
     def __init__(self, shape, h, method: str = "vgf", lam: float = 1.0, g0: float | None = None,
-                 device=None):
+                 device=None, dtype: str = "f32", direct: bool = False):
         self.lib = _lib.load()
         shape = tuple(int(s) for s in shape)
         h = tuple(float(x) for x in (h if np.ndim(h) else [h] * len(shape)))
         if len(shape) not in (2, 3) or len(h) != len(shape):
             raise ValueError("shape/h must have 2 or 3 entries")
+        if dtype not in DTYPES:
+            raise ValueError("dtype must be 'f32' or 'f64'")
         self.shape, self.h, self.method, self.dim = shape, h, method, len(shape)
+        self.dtype_name = dtype
+        self.dtype = DTYPES[dtype][1]
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         nz = shape[2] if self.dim == 3 else 0
         hz = h[2] if self.dim == 3 else 0.0
         with torch.cuda.device(self.device):
             handle = self.lib.fsp_plan_create_ex(shape[0], shape[1], nz, h[0], h[1], hz, METHODS[method],
-                                                 _lib.FSP_F32, float(lam), float("nan") if g0 is None else g0)
+                                                 DTYPES[dtype][0], float(lam), float("nan") if g0 is None else g0,
+                                                 _lib.FSP_PLAN_DIRECT if direct else 0)
             if not handle:
                 raise _lib.FspError(self.lib.fsp_last_error(), f"fsp_plan_create{shape}")
             self.handle = ctypes.c_void_p(handle)
@@ -105,16 +116,20 @@ class Plan:
     # ---------------------------------------------------------------- solve
     def _check_grid(self, t, name, lead=()):
         want = tuple(lead) + self.shape
-        if t.dtype != torch.float32 or not t.is_cuda or tuple(t.shape) != want or not t.is_contiguous():
-            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {want}")
+        if t.dtype != self.dtype or not t.is_cuda or tuple(t.shape) != want or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} CUDA tensor of shape {want}")
 
     def solve(self, rho, with_phi: bool = True, with_E: bool = True, phi=None, E=None, stream=None):
-        """phi, E for density rho (float32 CUDA tensor of the plan's shape)."""
+        """phi, E for density rho (CUDA tensor of the plan's shape and dtype)."""
         self._check_grid(rho, "rho")
+        if phi is not None:
+            self._check_grid(phi, "phi")
+        if E is not None:
+            self._check_grid(E, "E", (self.dim,))
         if with_phi and phi is None:
             phi = torch.empty_like(rho)
         if with_E and E is None:
-            E = torch.empty((self.dim,) + self.shape, dtype=torch.float32, device=rho.device)
+            E = torch.empty((self.dim,) + self.shape, dtype=self.dtype, device=rho.device)
         _lib.check(self.lib.fsp_solve(self.handle, _ptr(rho), _ptr(phi if with_phi else None),
                                       _ptr(E if with_E else None), _stream(stream)), "fsp_solve")
         return (phi if with_phi else None), (E if with_E else None)
@@ -125,7 +140,7 @@ class Plan:
         """E = -grad(phi) by centred differences (second-order one-sided at the faces)."""
         self._check_grid(phi, "phi")
         if E is None:
-            E = torch.empty((self.dim,) + self.shape, dtype=torch.float32, device=phi.device)
+            E = torch.empty((self.dim,) + self.shape, dtype=self.dtype, device=phi.device)
         _lib.check(self.lib.fsp_gradient_fd(self.handle, _ptr(phi), _ptr(E), _stream(stream)), "fsp_gradient_fd")
         return E
 
@@ -139,7 +154,7 @@ class Plan:
             self._check_grid(g_E, "g_E", (self.dim,))
         ref = g_phi if g_phi is not None else g_E
         if g_rho is None:
-            g_rho = torch.empty(self.shape, dtype=torch.float32, device=ref.device)
+            g_rho = torch.empty(self.shape, dtype=self.dtype, device=ref.device)
         _lib.check(self.lib.fsp_solve_adjoint(self.handle, _ptr(g_phi), _ptr(g_E), _ptr(g_rho), _stream(stream)),
                    "fsp_solve_adjoint")
         return g_rho
@@ -172,7 +187,7 @@ def solve_batched(plans, rhos, with_phi: bool = True, with_E: bool = True, strea
     """Independent solves over several plans (distinct plans, one workspace each)."""
     lib = _lib.load()
     phis = [torch.empty_like(r) if with_phi else None for r in rhos]
-    Es = [torch.empty((p.dim,) + p.shape, dtype=torch.float32, device=r.device) if with_E else None
+    Es = [torch.empty((p.dim,) + p.shape, dtype=p.dtype, device=r.device) if with_E else None
           for p, r in zip(plans, rhos)]
     for p, r in zip(plans, rhos):
         p._check_grid(r, "rho")
@@ -191,7 +206,7 @@ class Batch:
         self.lib = _lib.load()
         self.plans, self.rhos = list(plans), list(rhos)
         self.phis = [torch.empty_like(r) if with_phi else None for r in self.rhos]
-        self.Es = [torch.empty((p.dim,) + p.shape, dtype=torch.float32, device=r.device) if with_E else None
+        self.Es = [torch.empty((p.dim,) + p.shape, dtype=p.dtype, device=r.device) if with_E else None
                    for p, r in zip(self.plans, self.rhos)]
         h = self.lib.fsp_batch_create(_arr([p.handle for p in self.plans]), len(self.plans),
                                       _arr([_ptr(r) for r in self.rhos]),
@@ -245,10 +260,10 @@ class HostPipeline:
     def __init__(self, plan: Plan, depth: int = 2, with_phi: bool = True, with_E: bool = True):
         self.plan, self.depth, self.with_phi, self.with_E = plan, depth, with_phi, with_E
         dev = plan.device
-        self.rho = [torch.empty(plan.shape, dtype=torch.float32, device=dev) for _ in range(depth)]
-        self.phi = [torch.empty(plan.shape, dtype=torch.float32, device=dev) if with_phi else None
+        self.rho = [torch.empty(plan.shape, dtype=plan.dtype, device=dev) for _ in range(depth)]
+        self.phi = [torch.empty(plan.shape, dtype=plan.dtype, device=dev) if with_phi else None
                     for _ in range(depth)]
-        self.E = [torch.empty((plan.dim,) + plan.shape, dtype=torch.float32, device=dev) if with_E else None
+        self.E = [torch.empty((plan.dim,) + plan.shape, dtype=plan.dtype, device=dev) if with_E else None
                   for _ in range(depth)]
         self.s_in, self.s_run, self.s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
         self.loaded = [torch.cuda.Event() for _ in range(depth)]

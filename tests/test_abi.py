@@ -48,15 +48,19 @@ def test_error_strings(lib):
     ((32, 32, 32, 0.0, 0.1, 0.1, 1, 0), 1),          # zero spacing
     ((32, 32, 32, 0.1, 0.1, 0.1, 9, 0), 1),          # unknown method
     ((32, 32, 32, 0.1, 0.1, 0.1, 1, 7), 1),          # unknown dtype
-    ((32, 32, 32, 0.1, 0.1, 0.1, 1, 1), 2),          # FP64 solves not provided
-    ((33, 32, 32, 0.1, 0.1, 0.1, 1, 0), 2),          # 2n = 66 not covered
-    ((32, 32, 40, 0.1, 0.1, 0.1, 0, 0), 2),          # 2n = 80 not covered
+    ((513, 32, 32, 0.1, 0.1, 0.1, 1, 0), 2),         # 2n = 1026: no FFT pass, beyond the direct path
+    ((32, 32, 600, 0.1, 0.1, 0.1, 0, 1), 2),         # FP64 (direct path) beyond 512 cells
     ((1024, 32, 32, 0.1, 0.1, 0.1, 0, 0), 2),        # 3D axis beyond 2n = 1024
-    ((4096, 4097, 0, 0.1, 0.1, 0.0, 1, 0), 2),       # 2D odd contiguous axis
+    ((4096, 4097, 0, 0.1, 0.1, 0.0, 1, 0), 2),       # 2D odd contiguous axis beyond the direct path
 ])
 def test_plan_create_rejects(lib, args, code):
     assert lib.fsp_plan_create(*args) is None
     assert lib.fsp_last_error() == code
+
+
+def test_plan_create_ex_rejects_unknown_flags(lib):
+    assert lib.fsp_plan_create_ex(32, 32, 32, 0.1, 0.1, 0.1, 1, 0, 1.0, float("nan"), 2) is None
+    assert lib.fsp_last_error() == 1
 
 
 def test_null_arguments(lib):
