@@ -64,6 +64,12 @@ int supported_axis0(int N)
     }
 }
 
+// 1: 2D first-axis passes with 2 n0 >= 2048 run persistent with a cp.async
+// stage (p1_fwd_pst / p5_fwd_pst); 0: one CTA per column group (p1_fwd_blk / p5_fwd_blk).
+#ifndef FSP_LONG_STAGED
+#define FSP_LONG_STAGED 1
+#endif
+
 template <int N, int EE>
 static constexpr size_t smem_p1() { return (size_t)(N / 2 * TileCfg<N, EE>::C + TileCfg<N, EE>::EX) * sizeof(float2); }
 template <int N, int EE>
@@ -110,6 +116,11 @@ static int prep_one()
     } else {
         e |= cudaFuncSetAttribute(p1_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         e |= cudaFuncSetAttribute(p5_fwd_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if constexpr (!C::WIDE) {
+            const int sm = (int)LongStage<N>::SMEM;
+            e |= cudaFuncSetAttribute(p1_fwd_pst<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            e |= cudaFuncSetAttribute(p5_fwd_pst<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        }
     }
     return e;
 }
@@ -148,6 +159,18 @@ static int units_p5f(const PassArgs &a)
     else return units_col<N>(a);
 }
 
+// Persistent staged long columns (2D, BZ < 16): every item 2D with whole column groups.
+template <int N>
+static bool staged_fits(int kind, const PassArgs *items, int n)
+{
+    constexpr int BZ = ColCfg<N>::BZ;
+    for (int i = 0; i < n; ++i) {
+        const int cols = kind == PASS_P1F ? items[i].n2 / 2 : items[i].n2;
+        if (items[i].three_d || cols % BZ) return false;
+    }
+    return true;
+}
+
 // variant bits: 1 = 8 values per thread in the tiles (else 16); 2 = one CTA per SM
 template <int N, int EE, class Wk>
 static int tile_launch(int kind, const Wk &w, int var, cudaStream_t st)
@@ -175,6 +198,15 @@ static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
                 return (var & 1) ? tile_launch<N, 8>(kind, w, var, st) : tile_launch<N, 16>(kind, w, var, st);
             } else {
                 const int total = w.offs[w.nitems];
+                if constexpr (!ColCfg<N>::WIDE) {
+                    if (FSP_LONG_STAGED && staged_fits<N>(kind, w.item, w.nitems)) {
+                        const int grid = std::min(total, sm_count());
+                        if (kind == PASS_P1F)
+                            p1_fwd_pst<N, MAXI><<<grid, ColCfg<N>::THREADS, LongStage<N>::SMEM, st>>>(w);
+                        else p5_fwd_pst<N, MAXI><<<grid, ColCfg<N>::THREADS, LongStage<N>::SMEM, st>>>(w);
+                        return (int)cudaGetLastError();
+                    }
+                }
                 if (kind == PASS_P1F) p1_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
                 else p5_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
                 return (int)cudaGetLastError();

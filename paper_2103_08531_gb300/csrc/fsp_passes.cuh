@@ -620,6 +620,153 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
     }
 }
 
+// ------------------------------- persistent staged passes for long columns
+//
+// 2D problems with 2 n0 >= 2048 hold only BZ = 2..8 columns of the first axis
+// per CTA, one CTA per SM.  These persistent versions copy the next column
+// group's input rows into a shared-memory stage with cp.async while the
+// current group is transformed, so the (narrow, row-strided) loads overlap
+// the FFT instead of stalling it.  Layout: exchange buffer (ColCfg), then the
+// stage [rows][BZ] on a 16-byte boundary.
+template <int N>
+struct LongStage {
+    using C = ColCfg<N>;
+    static constexpr int OFF = (C::SPAN * C::BZ + 1) / 2 * 2;   // float2
+    static constexpr int ROWS = N / 2 + 1;
+    static constexpr size_t SMEM = (size_t)(OFF + ROWS * C::BZ) * sizeof(float2);
+    static_assert(!C::WIDE, "staged long columns are for BZ < 16");
+    // cp.async rows [0, rows) of BZ complex columns (row r at src + r * ld) into stage
+    static __device__ __forceinline__ void copy(float2 *stage, const float2 *src, size_t ld, int rows)
+    {
+        constexpr int CH = C::BZ / 2;   // 16-byte chunks per row
+        for (int c = threadIdx.x; c < rows * CH; c += C::THREADS) {
+            const int r = c / CH, q = c % CH;
+            cp_async16(stage + r * C::BZ + 2 * q, src + (size_t)r * ld + 2 * q);
+        }
+    }
+};
+
+// P1 (2D, 2 n0 >= 2048), persistent.  Unit: a group of BZ packed column pairs.
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_constant__ Work<MAXI> W)
+{
+    using C = ColCfg<N>;
+    using S = LongStage<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ, NH = N / 2;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    float2 *stage = smem + S::OFF;   // [NH][BZ] packed pairs
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int nw = W.count();
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const int z0 = 2 * BZ * ub;   // first real column
+        S::copy(stage, reinterpret_cast<const float2 *>(b.in[0] + z0), b.n2 / 2, NH);
+    };
+    int w = blockIdx.x;
+    if (w < nw) issue(w);
+    cp_async_commit();
+    const auto sm = C::view(smem, col);
+    for (; w < nw; w += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        FSP_UNIT(W, w, a, u);
+        const int z0 = 2 * (BZ * u + col);
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? stage[(j + r * T) * BZ + col] : make_float2(0.f, 0.f);
+        __syncthreads();
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
+        cp_async_commit();
+        line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+        for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r <= E / 2; ++r) {
+            const int k = j + r * T;
+            if (k <= NH) {
+                const float2 x = v[r];
+                const float2 m = sm.at(k == 0 ? 0 : N - k);
+                float4 o;
+                o.x = 0.5f * (x.x + m.x);
+                o.y = 0.5f * (x.y - m.y);
+                o.z = 0.5f * (x.y + m.y);
+                o.w = -0.5f * (x.x - m.x);
+                *reinterpret_cast<float4 *>(a.buf0 + iidx(a, k, 0, z0)) = o;
+            }
+        }
+        __syncthreads();   // the exchange buffer is reused by the next group
+    }
+    cp_async_wait_all();
+}
+
+// P5 (2D, 2 n0 >= 2048), persistent over (column group, stream) jobs: stream 0
+// is buf0 -> (phi, E0) by W = (1 + k0) P, stream 1 is buf1 -> E1.  The next
+// job's rows are staged while the current job is transformed.
+template <int N, int MAXI>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_constant__ Work<MAXI> W)
+{
+    using C = ColCfg<N>;
+    using S = LongStage<N>;
+    constexpr int E = C::E, T = C::T, BZ = C::BZ, NH = N / 2;
+    using RAD = typename Plan1D<N>::R;
+    extern __shared__ float2 smem[];
+    float2 *stage = smem + S::OFF;   // [NH + 1][BZ]
+    const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
+    const int nw = W.count();
+    // job t: unit blockIdx.x + (t / 2) gridDim.x, stream t % 2; next active job from t
+    auto next = [&](int t) -> int {
+        for (;; ++t) {
+            const int w = blockIdx.x + (t >> 1) * (int)gridDim.x;
+            if (w >= nw) return -1;
+            FSP_UNIT(W, w, b, ub);
+            if ((t & 1) ? b.out[2] != nullptr : (b.out[0] != nullptr || b.out[1] != nullptr)) return t;
+        }
+    };
+    auto issue = [&](int t) {
+        FSP_UNIT(W, blockIdx.x + (t >> 1) * (int)gridDim.x, b, ub);
+        const float2 *src = ((t & 1) ? b.buf1 : b.buf0) + BZ * ub;
+        S::copy(stage, src, b.n2, NH + 1);
+    };
+    int t = next(0);
+    if (t >= 0) issue(t);
+    cp_async_commit();
+    const auto sm = C::view(smem, col);
+    while (t >= 0) {
+        cp_async_wait_all();
+        __syncthreads();
+        FSP_UNIT(W, blockIdx.x + (t >> 1) * (int)gridDim.x, a, u);
+        const int z = BZ * u + col;
+        const bool s1 = (t & 1) != 0;
+        float *oa = s1 ? a.out[2] : a.out[0];
+        float *ob = s1 ? nullptr : a.out[1];
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int src = k <= NH ? k : N - k;
+            float2 p = stage[src * BZ + col];
+            if (k > NH) p.y = -p.y;
+            if (ob) p = (1.f + wave(k, NH, a.k0s)) * p;   // W = P + i (-i k0 P): Re -> phi, Im -> E0
+            v[r] = p;
+        }
+        __syncthreads();
+        const int tn = next(t + 1);
+        if (tn >= 0) issue(tn);
+        cp_async_commit();
+        line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r) {
+            const size_t g = gidx(a, j + r * T, 0, z);
+            if (oa) oa[g] = v[r].x;
+            if (ob) ob[g] = v[r].y;
+        }
+        t = tn;
+    }
+    cp_async_wait_all();
+}
+
 
 
 // =====================================================================
