@@ -102,7 +102,11 @@ struct ColCfg {
     static constexpr int BZ = (T * 16 <= 1024) ? 16 : (1024 / T);
     static constexpr int THREADS = T * BZ;
     static constexpr bool WIDE = BZ >= 16;
-    static constexpr int SPAN = RowSpan<N, 4>::value;   // per-column span when !WIDE
+    // Per-column span when !WIDE: at least RowSpan (one padding slot per 16
+    // positions), rounded up to SPAN = 16 / BZ (mod 16) so that the BZ columns a
+    // half-warp touches sit 32 / BZ banks apart and their exchanges do not
+    // collide (the columns are interleaved across lanes: tid -> (tid % BZ, tid / BZ)).
+    static constexpr int SPAN = (RowSpan<N, 4>::value + 15 - (16 / BZ) % 16) / 16 * 16 + (16 / BZ) % 16;
     static constexpr size_t SMEM = (size_t)(WIDE ? N * BZ : SPAN * BZ) * sizeof(float2);
     using View = typename std::conditional<WIDE, ColView, RowView<4>>::type;
     static __device__ __forceinline__ View view(float2 *smem, int col)
