@@ -304,7 +304,22 @@ enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // TW_SMEM: as TW_GATHER, but the caller has copied the whole table (main
 // part and gathered blocks) into shared memory and passes that copy.
 // TW_STABLE: as TW_TABLE, from a copy of the main table in shared memory.
-enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4 };
+// TW_QSMEM: a shared-memory copy of the first quarter of the table only
+// (N a multiple of 4): W^(m + N/4) = -i W^m, so W^m is the entry m mod N/4
+// turned by (-i)^(m div N/4).
+enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4, TW_QSMEM = 5 };
+
+// W_N^m (m < N) from the quarter table.
+template <int N>
+__device__ __forceinline__ float2 qtw(const float2 *tq, int m)
+{
+    constexpr int Q = N / 4;
+    const int qd = m / Q;
+    const float2 t = tq[m - qd * Q];
+    float2 r = (qd & 1) ? make_float2(t.y, -t.x) : t;   // times -i
+    if (qd & 2) r = make_float2(-r.x, -r.y);             // times -1
+    return r;
+}
 
 template <int TW>
 __device__ __forceinline__ float2 ldtw(const float2 *p)
@@ -373,7 +388,12 @@ struct NextOff {
 template <int N, int R, bool INV, int NS, int TW, int OFF>
 __device__ __forceinline__ void pass_twiddles(float2 *u, const float2 *__restrict__ tw, int k)
 {
-    if constexpr ((TW == TW_GATHER || TW == TW_SMEM) && NS < 32) {
+    if constexpr (TW == TW_QSMEM) {
+        static_assert(N % 4 == 0, "the quarter table needs N divisible by 4");
+        const int m = k * (N / (NS * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], qtw<N>(tw, r * m));
+    } else if constexpr ((TW == TW_GATHER || TW == TW_SMEM) && NS < 32) {
 #pragma unroll
         for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], ldtw<TW>(tw + N + OFF + r * NS + k));
     } else {

@@ -116,6 +116,12 @@ struct ColCfg {
     }
 };
 
+// Twiddle source of the long-line forward middle pass (TW_POW: 4 table loads
+// and products per radix-16 butterfly, fewer live registers than TW_TABLE).
+#ifndef FSP_ROW_TW
+#define FSP_ROW_TW TW_POW
+#endif
+
 template <int N>
 struct RowCfg {
     static constexpr int E = Plan1D<N>::E;
@@ -376,14 +382,14 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
         const bool act = line < lines;
         const int lc = act ? line : 0;
         const int kx = lc / a.rows1, row = lc % a.rows1;
-        const int n2 = a.n2;
+        constexpr int n2 = N / 2;   // every item of a length-N launch has n2 = N / 2
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = (r < E / 2 && act) ? stage[li * NH + j + r * T] : make_float2(0.f, 0.f);
         __syncthreads();
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
-        line_fft<N, E, false, true, RAD>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
         const float *Kr = krow(a, kx, row);
         if constexpr (C::SAVE) {
             float2 *sv = stage + LPC * NH + li * N;   // product spectrum of this line
@@ -394,7 +400,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
                 v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
                 sv[k] = v[r];
             }
-            line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
             if (act) {
                 float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
                     const float2 sk = sv[k];
                     v[r] = make_float2(kk * sk.y, -kk * sk.x);   // -i k2 (K rho^)
                 }
-                line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
                 if (act) {
                     float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
@@ -426,14 +432,14 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
                 const float kk = wave(k, n2, a.k2s);
                 q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
             }
-            line_fft<N, E, true, false, RAD>(v, j, a.tw2, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
             if (act) {
                 float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
                 for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
             }
             if (withE) {
-                line_fft<N, E, true, false, RAD>(q, j, a.tw2, sm);
+                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(q, j, a.tw2, sm);
                 if (act) {
                     float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
@@ -632,13 +638,33 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
 // current group is transformed, so the (narrow, row-strided) loads overlap
 // the FFT instead of stalling it.  Layout: exchange buffer (ColCfg), then the
 // stage [rows][BZ] on a 16-byte boundary.
+// Twiddle source of the staged long-column passes: TW_QSMEM (quarter table in
+// shared memory), TW_POW or TW_TABLE.
+#ifndef FSP_COL_TW
+#define FSP_COL_TW TW_TABLE
+#endif
+
 template <int N>
 struct LongStage {
     using C = ColCfg<N>;
     static constexpr int OFF = (C::SPAN * C::BZ + 1) / 2 * 2;   // float2
     static constexpr int ROWS = N / 2 + 1;
-    static constexpr size_t SMEM = (size_t)(OFF + ROWS * C::BZ) * sizeof(float2);
+    static constexpr int TWOFF = OFF + ROWS * C::BZ;             // quarter table (TW_QSMEM)
+    static constexpr int TWQ = FSP_COL_TW == TW_QSMEM ? N / 4 : 0;
+    static constexpr size_t SMEM = (size_t)(TWOFF + TWQ) * sizeof(float2);
     static_assert(!C::WIDE, "staged long columns are for BZ < 16");
+    // Every thread of the block calls this once, before its first transform.
+    static __device__ __forceinline__ const float2 *twiddles(float2 *smem, const float2 *gtw)
+    {
+        if constexpr (TWQ > 0) {
+            float2 *t = smem + TWOFF;
+            for (int i = threadIdx.x; i < TWQ; i += C::THREADS) t[i] = gtw[i];
+            __syncthreads();
+            return t;
+        } else {
+            return gtw;
+        }
+    }
     // cp.async rows [0, rows) of BZ complex columns (row r at src + r * ld) into stage
     static __device__ __forceinline__ void copy(float2 *stage, const float2 *src, size_t ld, int rows)
     {
@@ -662,6 +688,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_co
     float2 *stage = smem + S::OFF;   // [NH][BZ] packed pairs
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
     const int nw = W.count();
+    const float2 *tw = S::twiddles(smem, W.item[0].tw0);   // the table depends on N only
     auto issue = [&](int w) {
         FSP_UNIT(W, w, b, ub);
         const int z0 = 2 * BZ * ub;   // first real column
@@ -682,7 +709,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_co
         __syncthreads();
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
-        line_fft<N, E, false, true, RAD>(v, j, a.tw0, sm);
+        line_fft<N, E, false, true, RAD, typename C::View, SYNC_BLOCK, FSP_COL_TW>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
         __syncthreads();
@@ -719,6 +746,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_co
     float2 *stage = smem + S::OFF;   // [NH + 1][BZ]
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
     const int nw = W.count();
+    const float2 *tw = S::twiddles(smem, W.item[0].tw0);   // the table depends on N only
     // job t: unit blockIdx.x + (t / 2) gridDim.x, stream t % 2; next active job from t
     auto next = [&](int t) -> int {
         for (;; ++t) {
@@ -759,7 +787,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_co
         const int tn = next(t + 1);
         if (tn >= 0) issue(tn);
         cp_async_commit();
-        line_fft<N, E, true, false, RAD>(v, j, a.tw0, sm);
+        line_fft<N, E, true, false, RAD, typename C::View, SYNC_BLOCK, FSP_COL_TW>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E / 2; ++r) {
             const size_t g = gidx(a, j + r * T, 0, z);
