@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
 // Twiddle source of the staged long-column passes: TW_QSMEM (quarter table in
 // shared memory), TW_POW or TW_TABLE.
 #ifndef FSP_COL_TW
-#define FSP_COL_TW TW_TABLE
+#define FSP_COL_TW TW_POW
 #endif
 
 template <int N>
