@@ -384,6 +384,62 @@ def test_autotune_measures_and_writes_cache(fsp, tmp_path):
     plan.autotune(path, 0)
 
 
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("direct", [False, True])
+@pytest.mark.parametrize("name,shape,h", [SMALL[1], SMALL[3]])
+def test_zero_density_gives_zero(fsp, name, shape, h, direct):
+    """rho = 0: every output is exactly zero (no stale workspace contents leak in)."""
+    plan = fsp.Plan(shape, h, "vgf", direct=direct)
+    plan.solve(torch.from_numpy(_mixture(shape, h, 5).rho(np.float32)).cuda())   # dirty the workspace first
+    phi, E = plan.solve(torch.zeros(shape, device="cuda"))
+    torch.cuda.synchronize()
+    assert int(torch.count_nonzero(phi)) == 0 and int(torch.count_nonzero(E)) == 0
+
+
+@pytest.mark.parametrize("method", ["vgf", "he"])
+@pytest.mark.parametrize("name,shape,h,cell", [("cube32", (32, 32, 32), (2 / 32,) * 3, (5, 17, 30)),
+                                               ("aniso", (32, 64, 96), (0.03, 0.02, 0.011), (31, 0, 40)),
+                                               ("2d", (64, 128), (0.02, 0.011), (10, 127))])
+def test_point_charge_reproduces_the_kernel(fsp, oracle_mod, method, name, shape, h, cell):
+    """A unit point charge (rho = 1 / prod(h) at one cell) gives phi_i = g(x_i - x_c): the
+    oracle's real-space kernel itself, read by offset -- no oracle FFT is involved."""
+    rho = np.zeros(shape, dtype=np.float32)
+    rho[cell] = 1.0 / np.prod(h)
+    phi, _ = fsp.Plan(shape, h, method).solve(torch.from_numpy(rho).cuda(), with_E=False)
+    g = oracle_mod.kernel(method, list(shape), h)
+    idx = np.ix_(*[(np.arange(n) - c) % (2 * n) for n, c in zip(shape, cell)])
+    assert rel(phi.cpu(), g[idx]) <= TOL
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", TOL), ("f64", 1e-11)])
+@pytest.mark.parametrize("shape,h", [((1, 1, 1), (0.1, 0.2, 0.3)), ((1, 5, 2), (0.1, 0.05, 0.2)),
+                                     ((3, 1), (0.1, 0.3)), ((2, 2), (0.2, 0.2))])
+def test_degenerate_sizes(fsp, oracle_mod, shape, h, dtype, tol):
+    """One or two cells per axis (padded lengths 2 and 4) through the direct-sum path."""
+    rng = np.random.default_rng(11)
+    np_dt = np.float32 if dtype == "f32" else np.float64
+    rho = rng.standard_normal(shape).astype(np_dt)
+    phi, E = fsp.Plan(shape, h, "vgf", dtype=dtype).solve(torch.from_numpy(rho).cuda())
+    p_ref, E_ref = oracle_mod.solve_with_kernel(oracle_mod.kernel_vgf(list(shape), h), rho.astype(np.float64), h)
+    assert rel(phi.cpu(), p_ref) <= tol
+    if np.max(np.abs(E_ref)) > 0:
+        assert np.max(np.abs(E.cpu().numpy() - E_ref)) <= tol * max(np.max(np.abs(E_ref)), np.max(np.abs(p_ref)))
+
+
+def test_largest_3d_axes_sampled(fsp, oracle_mod):
+    """2n = 1024 on the first two axes (the largest 3D passes: column tiles of 1024 points on
+    axes 0 and 1): HE phi at 32 sampled cells against the brute-force sum."""
+    shape, h = (512, 512, 32), (1 / 256, 1 / 256, 1 / 16)
+    prob = _mixture(shape, h, seed=12)
+    _, rho32, phi, E = gpu_solve(fsp, prob, "he")
+    g = oracle_mod.kernel_he(list(shape), h)
+    pts = np.random.default_rng(13).integers(0, phi.size, size=32)
+    ref = oracle_mod.direct_phi_at(g, rho32.astype(np.float64), h, pts)
+    assert np.max(np.abs(phi.ravel()[pts] - ref)) <= TOL * np.max(np.abs(phi))
+    assert np.all(np.isfinite(E))
+
+
 # ------------------------------------------------------------ full sizes
 
 def test_full_size_256_vgf_against_oracle(fsp, oracle_mod):
