@@ -159,6 +159,7 @@ void fsp_batch_destroy(fsp_batch *batch);
  * its stream just before pass i, and events[passes] after the last pass
  * (passes = 5 in 3D, 3 in 2D; count must be >= passes + 1).  events = NULL or
  * count = 0 turns it off.  The array is copied; the events stay the caller's.
+ * Plans on the direct-sum path have no such passes: FSP_ERR_INVALID.
  */
 int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count);
 

@@ -278,7 +278,7 @@ extern "C" int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int
         return set_err(FSP_OK);
     }
     const int need = p.three_d ? 6 : 4;
-    if (count < need || count > 8) return set_err(FSP_ERR_INVALID);
+    if (p.direct || count < need || count > 8) return set_err(FSP_ERR_INVALID);   // direct plans have no passes
     for (int i = 0; i < count; ++i) {
         if (!events[i]) return set_err(FSP_ERR_INVALID);
         p.pass_ev[i] = (cudaEvent_t)events[i];

@@ -155,40 +155,6 @@ __device__ __forceinline__ void dft16(float2 *v)
     }
 }
 
-// exp(-/+ 2 pi i u / 32), u = 1..15
-template <bool INV>
-__device__ __forceinline__ float2 w32(float2 a, int u)
-{
-    // cos and sin of u pi / 16
-    const float c[9] = {1.0f, 0.98078528040323044f, 0.92387953251128674f, 0.83146961230254524f,
-                        0.70710678118654752f, 0.55557023301960218f, 0.38268343236508977f, 0.19509032201612827f, 0.0f};
-    if (u == 8) return rot<INV>(a);
-    if (u % 2 == 0) return w16<INV>(a, u / 2);
-    const float cs = u < 8 ? c[u] : -c[16 - u];
-    const float sn = u < 8 ? c[8 - u] : c[u - 8];
-    return cmul_dir<INV>(a, make_float2(cs, -sn));
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft32(float2 *v)
-{
-    float2 e[16], o[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        e[i] = v[2 * i];
-        o[i] = v[2 * i + 1];
-    }
-    dft16<INV>(e);
-    dft16<INV>(o);
-#pragma unroll
-    for (int u = 1; u < 16; ++u) o[u] = w32<INV>(o[u], u);
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        v[u] = e[u] + o[u];
-        v[u + 16] = e[u] - o[u];
-    }
-}
-
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 *v)
 {
@@ -197,7 +163,6 @@ __device__ __forceinline__ void dft(float2 *v)
     else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 8) dft8<INV>(v);
     else if constexpr (R == 16) dft16<INV>(v);
-    else if constexpr (R == 32) dft32<INV>(v);
     else static_assert(R == 2, "unsupported radix");
 }
 
@@ -239,20 +204,6 @@ __device__ __forceinline__ void dft_half_in(float2 *v)
         dft8<INV>(b);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            v[2 * u] = a[u];
-            v[2 * u + 1] = b[u];
-        }
-    } else if constexpr (R == 32) {
-        float2 a[16], b[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            a[r] = v[r];
-            b[r] = (r == 0) ? v[0] : w32<INV>(v[r], r);
-        }
-        dft16<INV>(a);
-        dft16<INV>(b);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
             v[2 * u] = a[u];
             v[2 * u + 1] = b[u];
         }
@@ -600,9 +551,5 @@ template <> struct Plan16<192> { static constexpr int E = 12; using R = Radices<
 template <> struct Plan16<256> { static constexpr int E = 16; using R = Radices<16, 16>; };
 template <> struct Plan16<512> { static constexpr int E = 16; using R = Radices<16, 16, 2>; };
 
-// 32 values per thread: one shared-memory exchange per 512-point transform.
-template <int N>
-struct Plan32 : Plan16<N> {};
-template <> struct Plan32<512> { static constexpr int E = 32; using R = Radices<32, 16>; };
 
 } // namespace fsp

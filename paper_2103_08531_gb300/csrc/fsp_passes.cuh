@@ -1279,9 +1279,6 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
 #define FSP_P3_TW TW_SMEM
 #endif
 
-#ifndef FSP_P3_E32
-#define FSP_P3_E32 0
-#endif
 // Optional minimum resident blocks for the middle pass.  Leave unset: a
 // bound of 1 lets the compiler take far more registers (measured slower).
 #ifdef FSP_P3_MINB
@@ -1290,7 +1287,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
 #define FSP_P3_BOUNDS(t) __launch_bounds__(t)
 #endif
 template <int N>
-using P3Plan = typename std::conditional<FSP_P3_E32 != 0, Plan32<N>, Plan16<N>>::type;
+using P3Plan = Plan16<N>;
 
 template <int N>
 struct WarpCfg {

@@ -200,3 +200,13 @@ def test_f64_vgf_converges_spectrally_he_like_h2(fsp):
     assert err[("vgf", 48)] < 1e-6
     for n in (12, 24, 48):
         assert err[("vgf", n)] < err[("he", n)]
+
+
+def test_direct_plan_rejects_pass_events(fsp):
+    """Per-pass timing events belong to the FFT passes; a direct-path plan refuses them."""
+    plan = fsp.Plan((13, 17, 11), (0.05, 0.04, 0.06), "vgf")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in evs:
+        e.record()
+    with pytest.raises(fsp.FspError):
+        plan.set_pass_events(evs)
