@@ -180,10 +180,10 @@ static int tile_launch(int kind, const Wk &w, int var, cudaStream_t st)
     const int sms = sm_count();
     if (kind == PASS_P1F) {
         const int cap = sms * ((var & 2) ? 1 : Occ0<N, MAXI, EE>::p1);
-        p1_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p1<N, EE>(), st>>>(w);
+        return launch_pdl(p1_fwd<N, MAXI, EE>, std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p1<N, EE>(), st, w);
     } else {
         const int cap = sms * ((var & 2) ? 1 : Occ0<N, MAXI, EE>::p5);
-        p5_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p5<N, EE>(), st>>>(w);
+        return launch_pdl(p5_fwd<N, MAXI, EE>, std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p5<N, EE>(), st, w);
     }
     return (int)cudaGetLastError();
 }

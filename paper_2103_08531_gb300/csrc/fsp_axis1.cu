@@ -150,10 +150,10 @@ static int tile_launch(int kind, const Wk &w, int flag, int var, cudaStream_t st
     const int sms = sm_count();
     if (kind == PASS_P2F) {
         const int cap = sms * ((var & 2) ? 1 : Occ1<N, MAXI, EE>::p2);
-        p2_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p2<N, EE>(), st>>>(w);
+        return launch_pdl(p2_fwd<N, MAXI, EE>, std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p2<N, EE>(), st, w);
     } else {
         const int cap = sms * ((var & 2) ? 1 : Occ1<N, MAXI, EE>::p4);
-        p4_fwd<N, MAXI, EE><<<std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p4<N, EE>(), st>>>(w, flag);
+        return launch_pdl(p4_fwd<N, MAXI, EE>, std::min(total, cap), TileCfg<N, EE>::THREADS, smem_p4<N, EE>(), st, w, flag);
     }
     return (int)cudaGetLastError();
 }

@@ -141,11 +141,11 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
             // variant bit 2: one CTA per SM (else as many as fit)
             const bool one = (var & 2) != 0;
             if (kind == PASS_P3F && MAXI == 1 && FSP_P3_ONE)
-                p3_fwd1<N><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3one)), C::THREADS, C::SMEM, st>>>(
-                    w.item[0], flag);
+                return launch_pdl(p3_fwd1<N>, std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3one)), C::THREADS,
+                                  C::SMEM, st, w.item[0], flag);
             else if (kind == PASS_P3F)
-                p3_fwd<N, MAXI><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3)), C::THREADS, C::SMEM, st>>>(
-                    w, flag);
+                return launch_pdl(p3_fwd<N, MAXI>, std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3)), C::THREADS,
+                                  C::SMEM, st, w, flag);
             else
                 p3_adj<N, MAXI><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3a)), C::THREADS, C::SMEM, st>>>(
                     w, flag);

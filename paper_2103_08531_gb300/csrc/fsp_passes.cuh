@@ -85,6 +85,29 @@ struct Work {
 };
 constexpr int BATCH_MAX = 32;   // items per batched launch
 
+// Programmatic dependent launch.  The forward passes are launched with the
+// programmatic stream-serialization attribute, so a pass's CTAs may be
+// scheduled while the previous pass is still finishing.  Each such pass
+// releases its own dependents at once (pdl_trigger) and waits for the
+// previous grid to complete, with its writes visible, before it touches
+// global memory (pdl_wait).  Both are no-ops for a launch without the
+// attribute.
+#ifndef FSP_PDL
+#define FSP_PDL 1
+#endif
+__device__ __forceinline__ void pdl_trigger()
+{
+#if FSP_PDL
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_wait()
+{
+#if FSP_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 #define FSP_UNIT(W, w, a, u)                  \
     const int it_##u = (W).find(w);           \
     const PassArgs &a = (W).item[it_##u];     \
@@ -886,6 +909,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p1_fwd(const __grid_c
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *stage = smem, *ex = smem + NH * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
     const int nw = W.count();
@@ -896,6 +920,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p1_fwd(const __grid_c
         issue_rows<CC>(stage, a.in[0] + gidx(a, 0, y, z0), (size_t)a.n1 * a.n2 * sizeof(float), NH, tid, C::THREADS);
     };
     int w = blockIdx.x;
+    pdl_wait();   // the previous pass's output (and its reads of our outputs) are complete
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
@@ -944,6 +969,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p2_fwd(const __grid_c
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *stage = smem, *ex = smem + NH * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
     const int nw = W.count();
@@ -954,6 +980,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p2_fwd(const __grid_c
         issue_rows<CC>(stage, a.buf1 + iidx(a, kx, 0, z0), (size_t)a.n2 * sizeof(float2), NH, tid, C::THREADS);
     };
     int w = blockIdx.x;
+    pdl_wait();   // the previous pass's output (and its reads of our outputs) are complete
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
@@ -987,6 +1014,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p4_fwd(const __grid_c
     constexpr int E = C::E, T = C::T;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *st0 = smem, *st1 = smem + N * CC, *ex = smem + 2 * N * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
     const int nw = W.count();
@@ -999,6 +1027,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p4_fwd(const __grid_c
         if (withE) issue_rows<CC>(st1, a.buf1 + iidx(a, kx, 0, z0), rs, N, tid, C::THREADS);
     };
     int w = blockIdx.x;
+    pdl_wait();   // the previous pass's output (and its reads of our outputs) are complete
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
@@ -1048,6 +1077,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_c
     constexpr int E = C::E, T = C::T, NH = N / 2, ROWS = N / 2 + 1;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *sA = smem, *sB = smem + ROWS * CC, *sC = smem + 2 * ROWS * CC, *ex = smem + 3 * ROWS * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
     const int nw = W.count();
@@ -1067,6 +1097,7 @@ __global__ void __launch_bounds__(TileCfg<N, EE>::THREADS) p5_fwd(const __grid_c
         }
     };
     int w = blockIdx.x;
+    pdl_wait();   // the previous pass's output (and its reads of our outputs) are complete
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
@@ -1331,6 +1362,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
     constexpr int n2 = N / 2;   // every item of a length-N launch has n2 = N / 2
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
     // (the single-item bound is computed from the geometry: the register
@@ -1339,6 +1371,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
     const int gstride = gridDim.x * C::WARPS;
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
     const float2 *tw = C::twiddles(smem, W.item[0].tw2);   // the table depends on N only
+    pdl_wait();
     int g = blockIdx.x * C::WARPS + warp;
     float2 pv[E / 2];
     auto fetch = [&](int gg) {
@@ -1405,6 +1438,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     constexpr int n2 = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
     const int lines = (a.n0 + 1) * a.rows1;
@@ -1412,6 +1446,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     const int gstride = gridDim.x * C::WARPS;
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
     const float2 *tw = C::twiddles(smem, a.tw2);
+    pdl_wait();
     int g = blockIdx.x * C::WARPS + warp;
     float2 pv[E / 2];   // the next line's pruned input, prefetched into registers
     auto fetch = [&](int gg) {
@@ -1513,6 +1548,25 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
         }
     }
+}
+
+// Launch a pass with the programmatic stream-serialization attribute (see
+// pdl_trigger / pdl_wait); the kernel must call pdl_wait before its first
+// global-memory access.
+template <class Kern, class... Args>
+inline int launch_pdl(Kern kern, int grid, int threads, size_t smem, cudaStream_t st, const Args &...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = FSP_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 } // namespace fsp
