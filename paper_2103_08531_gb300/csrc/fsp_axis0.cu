@@ -202,9 +202,8 @@ static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
                     if (FSP_LONG_STAGED && staged_fits<N>(kind, w.item, w.nitems)) {
                         const int grid = std::min(total, sm_count());
                         if (kind == PASS_P1F)
-                            p1_fwd_pst<N, MAXI><<<grid, ColCfg<N>::THREADS, LongStage<N>::SMEM, st>>>(w);
-                        else p5_fwd_pst<N, MAXI><<<grid, ColCfg<N>::THREADS, LongStage<N>::SMEM, st>>>(w);
-                        return (int)cudaGetLastError();
+                            return launch_pdl_if(kLongPdl<N>, p1_fwd_pst<N, MAXI>, grid, ColCfg<N>::THREADS, LongStage<N>::SMEM, st, w);
+                        return launch_pdl_if(kLongPdl<N>, p5_fwd_pst<N, MAXI>, grid, ColCfg<N>::THREADS, LongStage<N>::SMEM, st, w);
                     }
                 }
                 if (kind == PASS_P1F) p1_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);
@@ -218,9 +217,8 @@ static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
             return chunked(items, n, units_p5f<N>, [&](auto &w) {   // (y, C-column tile) units
                 constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
                 const int total = w.offs[w.nitems];
-                p1_adj_t<N, MAXI><<<std::min(total, sm_count() * OccA0<N, MAXI>::p1a), TileCfg<N>::THREADS,
-                                    smem_p1a<N>(), st>>>(w);
-                return (int)cudaGetLastError();
+                return launch_pdl(p1_adj_t<N, MAXI>, std::min(total, sm_count() * OccA0<N, MAXI>::p1a),
+                                  TileCfg<N>::THREADS, smem_p1a<N>(), st, w);
             });
         } else {
             return chunked(items, n, units_col<N>, [&](auto &w) {

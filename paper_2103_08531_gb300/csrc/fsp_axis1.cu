@@ -180,9 +180,8 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
                 return chunked(items, n, units_tile<N>, [&](auto &w) {
                     constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
                     const int total = w.offs[w.nitems];
-                    p2_adj_t<N, MAXI><<<std::min(total, sm_count() * OccA1<N, MAXI>::p2a), TileCfg<N>::THREADS,
-                                        smem_p2a<N>(), st>>>(w);
-                    return (int)cudaGetLastError();
+                    return launch_pdl(p2_adj_t<N, MAXI>, std::min(total, sm_count() * OccA1<N, MAXI>::p2a),
+                                      TileCfg<N>::THREADS, smem_p2a<N>(), st, w);
                 });
             }
         }

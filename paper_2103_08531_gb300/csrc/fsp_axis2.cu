@@ -147,13 +147,13 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
                 return launch_pdl(p3_fwd<N, MAXI>, std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3)), C::THREADS,
                                   C::SMEM, st, w, flag);
             else
-                p3_adj<N, MAXI><<<std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3a)), C::THREADS, C::SMEM, st>>>(
-                    w, flag);
+                return launch_pdl(p3_adj<N, MAXI>, std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3a)), C::THREADS,
+                                  C::SMEM, st, w, flag);
         } else {
             using C = RowCfg<N>;
             if (kind == PASS_P3F)
-                p3_fwd_blk<N, MAXI><<<std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::p3)), C::THREADS,
-                                      C::SMEM_STAGED, st>>>(w, flag);
+                return launch_pdl_if(kLongPdl<N>, p3_fwd_blk<N, MAXI>, std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::p3)),
+                                  C::THREADS, C::SMEM_STAGED, st, w, flag);
             else p3_adj_blk<N, MAXI><<<total, C::THREADS, C::SMEM, st>>>(w, flag);
         }
         return (int)cudaGetLastError();

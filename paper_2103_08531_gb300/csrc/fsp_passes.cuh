@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
     constexpr int E = C::E, T = C::T, LPC = C::LPC, NH = N / 2;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *stage = smem + C::STAGE_OFF;   // LPC x NH complex, 16-byte aligned
     const int li = threadIdx.x / T, j = threadIdx.x % T;
     const int nw = W.count();
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
         for (int c = threadIdx.x; c < chunks; c += C::THREADS) cp_async16(stage + 2 * c, src + 2 * c);
     };
     int w = blockIdx.x;
+    pdl_wait();
     if (w < nw) issue(w);
     cp_async_commit();
     for (; w < nw; w += gridDim.x) {
@@ -708,6 +710,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_co
     constexpr int E = C::E, T = C::T, BZ = C::BZ, NH = N / 2;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *stage = smem + S::OFF;   // [NH][BZ] packed pairs
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
     const int nw = W.count();
@@ -718,6 +721,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_co
         S::copy(stage, reinterpret_cast<const float2 *>(b.in[0] + z0), b.n2 / 2, NH);
     };
     int w = blockIdx.x;
+    pdl_wait();
     if (w < nw) issue(w);
     cp_async_commit();
     const auto sm = C::view(smem, col);
@@ -766,6 +770,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_co
     constexpr int E = C::E, T = C::T, BZ = C::BZ, NH = N / 2;
     using RAD = typename Plan1D<N>::R;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *stage = smem + S::OFF;   // [NH + 1][BZ]
     const int col = threadIdx.x % BZ, j = threadIdx.x / BZ;
     const int nw = W.count();
@@ -785,6 +790,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_co
         S::copy(stage, src, b.n2, NH + 1);
     };
     int t = next(0);
+    pdl_wait();
     if (t >= 0) issue(t);
     cp_async_commit();
     const auto sm = C::view(smem, col);
@@ -1168,6 +1174,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_adj_t(const __grid_con
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float *stage = reinterpret_cast<float *>(smem);            // [4][NH][CC] floats
     float2 *ex = smem + 2 * NH * CC;                            // after 4 * NH * CC floats
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
@@ -1183,6 +1190,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p1_adj_t(const __grid_con
                                    tid, C::THREADS);
     };
     int w = blockIdx.x;
+    pdl_wait();
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
@@ -1255,6 +1263,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     float2 *st0 = smem, *st1 = smem + N * CC, *ex = smem + (N + NH) * CC;
     const int tid = threadIdx.x, col = tid % CC, j = tid / CC;
     const int nw = W.count();
@@ -1267,6 +1276,7 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
         issue_rows<CC>(st1, a.buf1 + iidx(a, kx, 0, z0), rs, NH, tid, C::THREADS);
     };
     int w = blockIdx.x;
+    pdl_wait();
     if (w < nw) issue(w);
     cp_async_commit();
     ColView sm{ex + col, CC};
@@ -1505,12 +1515,14 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
     using RAD = typename C::RAD;
     extern __shared__ float2 smem[];
+    pdl_trigger();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
     const int nw = W.count();
     constexpr int n2 = N / 2;   // every item of a length-N launch has n2 = N / 2
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
     const float2 *tw = C::twiddles(smem, W.item[0].tw2);   // the table depends on N only
+    pdl_wait();
     for (int g = blockIdx.x * C::WARPS + warp; g < nw; g += gridDim.x * C::WARPS) {
         FSP_UNIT(W, g, a, u);
         const int lines = (a.n0 + 1) * a.rows1;
@@ -1550,11 +1562,11 @@ __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_const
     }
 }
 
-// Launch a pass with the programmatic stream-serialization attribute (see
-// pdl_trigger / pdl_wait); the kernel must call pdl_wait before its first
-// global-memory access.
+// Launch a pass with the programmatic stream-serialization attribute when
+// pdl (see pdl_trigger / pdl_wait); the kernel must call pdl_wait before its
+// first global-memory access.
 template <class Kern, class... Args>
-inline int launch_pdl(Kern kern, int grid, int threads, size_t smem, cudaStream_t st, const Args &...args)
+inline int launch_pdl_if(bool pdl, Kern kern, int grid, int threads, size_t smem, cudaStream_t st, const Args &...args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1563,10 +1575,22 @@ inline int launch_pdl(Kern kern, int grid, int threads, size_t smem, cudaStream_
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = FSP_PDL;
+    attr[0].val.programmaticStreamSerializationAllowed = FSP_PDL && pdl;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return (int)cudaLaunchKernelEx(&cfg, kern, args...);
 }
+
+template <class Kern, class... Args>
+inline int launch_pdl(Kern kern, int grid, int threads, size_t smem, cudaStream_t st, const Args &...args)
+{
+    return launch_pdl_if(true, kern, grid, threads, smem, st, args...);
+}
+
+// Long lines (2n >= 2048) gain from the early scheduling while a pass is short
+// (2n = 2048: 1024^2 solves -11%) and lose once it is long (2n = 8192: 4096^2
+// +1.2%, measured), so their launches use it below 2n = 8192 only.
+template <int N>
+constexpr bool kLongPdl = N < 8192;
 
 } // namespace fsp
