@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import math
+import platform
 import os
 import statistics
 import subprocess
@@ -195,12 +196,38 @@ def oracle_sample(n=128, repeats=1):
     return times, scale, oracle.threads()
 
 
-def cpu_baseline_block(n=128):
+def cpu_model() -> str:
+    """The host CPU's name as the kernel reports it (x86 'model name', else the Arm part number)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.processor() or "unknown"
+    for key in ("model name", "Model Name", "CPU part"):
+        for line in info:
+            if line.startswith(key):
+                return f"{key}: {line.split(':', 1)[1].strip()}"
+    return platform.machine()
+
+
+def cpu_baseline_block(n=128, n1=64):
+    """The oracle on all host threads at n^3, and on one thread at n1^3, both scaled to 256^3."""
+    import oracle
     times, scale, cores = oracle_sample(n)
     t = min(times)
+    prev = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        t1s, scale1, _ = oracle_sample(n1)
+    finally:
+        oracle.set_threads(prev)
+    t1 = min(t1s)
     return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one FP64 oracle phi+E solve of the same 8-Gaussian mixture at {n}^3 "
-                      f"({t:.2f} s), scaled to 256^3 by the N^3 log N work ratio {scale:.2f}"}
+                      f"({t:.2f} s), scaled to 256^3 by the N^3 log N work ratio {scale:.2f}",
+            "cpu": cpu_model(),
+            "single_thread": {"value": 1.0 / (t1 * scale1), "unit": UNIT, "cores": 1,
+                              "sample": f"the same solve at {n1}^3 on one thread ({t1:.2f} s), "
+                                        f"scaled by {scale1:.2f}"}}
 
 
 def run_reference(args):
