@@ -202,10 +202,13 @@ def cpu_model() -> str:
         info = open("/proc/cpuinfo").read().splitlines()
     except OSError:
         return platform.processor() or "unknown"
+    arm_parts = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+                 "0xd49": "Arm Neoverse-N2"}
     for key in ("model name", "Model Name", "CPU part"):
         for line in info:
             if line.startswith(key):
-                return f"{key}: {line.split(':', 1)[1].strip()}"
+                val = line.split(":", 1)[1].strip()
+                return arm_parts.get(val, f"{key}: {val}")
     return platform.machine()
 
 
