@@ -1,0 +1,67 @@
+"""Host-side pieces of bench.py that decide what the JSON line reports (CPU only).
+
+The algorithmic byte counts are the roofline denominators, so they are pinned
+here against the pipeline written out by hand (what each pass must read and
+write at least); the traffic figure is only reported for the sources it was
+measured on; the CPU baseline block carries the fields the report needs.
+"""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_pass_bytes_at_256_cubed():
+    """Per pass, counted by hand at 256^3 (complex 8 B, real 4 B):
+    P1 reads rho (256^3 real) and writes one half spectrum Z = 257 x 256 x 256 complex;
+    P2 reads Z and writes it padded to 512 rows (2Z); P3 reads 2Z and the 257^3 kernel
+    octant and writes two 2Z streams; P4 reads those and writes three Z; P5 reads them and
+    writes phi and three field components (4 x 256^3 real)."""
+    n = 256
+    Z = 257 * 256 * 256 * 8
+    cells = n ** 3
+    want = {
+        "p1_fwd": 4 * cells + Z,
+        "p2_fwd": Z + 2 * Z,
+        "p3_fwd": 2 * Z + 4 * 257 ** 3 + 2 * 2 * Z,
+        "p4_fwd": 2 * 2 * Z + 3 * Z,
+        "p5_fwd": 3 * Z + 4 * 4 * cells,
+    }
+    got = bench.pass_bytes((n, n, n), True)
+    assert got == want
+    assert sum(got.values()) == 3098283012
+    # about 184 n^3, the figure the roofline fraction is quoted against
+    assert abs(sum(got.values()) / n ** 3 - 184) < 1.0
+
+
+def test_pass_bytes_phi_only_is_smaller():
+    full = bench.pass_bytes((64, 64, 64), True)
+    phi = bench.pass_bytes((64, 64, 64), False)
+    assert all(phi[k] <= full[k] for k in full) and sum(phi.values()) < sum(full.values())
+
+
+def test_traffic_is_reported_only_for_the_measured_sources(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    (prof / "traffic.json").write_text(json.dumps({"vgf256": {"p3_fwd": {"dram_bytes": 123, "source_hash": "abc"}}}))
+    assert bench.ncu_traffic("p3_fwd", "vgf256") == 123
+    (prof / "traffic.json").write_text(json.dumps({"vgf256": {"p3_fwd": {"dram_bytes": 123, "source_hash": "old"}}}))
+    assert bench.ncu_traffic("p3_fwd", "vgf256") is None
+    assert bench.ncu_traffic("p4_fwd", "vgf256") is None
+
+
+def test_cpu_baseline_block_fields():
+    pytest.importorskip("oracle")
+    b = bench.cpu_baseline_block(16, 16)
+    for key in ("value", "unit", "cores", "kind", "sample", "cpu", "single_thread"):
+        assert key in b
+    assert b["kind"] == "oracle" and b["cores"] >= 1 and b["value"] > 0
+    assert b["single_thread"]["cores"] == 1 and b["single_thread"]["value"] > 0
