@@ -65,3 +65,19 @@ def test_cpu_baseline_block_fields():
         assert key in b
     assert b["kind"] == "oracle" and b["cores"] >= 1 and b["value"] > 0
     assert b["single_thread"]["cores"] == 1 and b["single_thread"]["value"] > 0
+
+
+def test_padded_fft_context_solve_matches_oracle():
+    """The torch.fft context solve in bench.py is the same discrete convolution as the oracle's."""
+    import numpy as np
+    import torch
+    oracle = pytest.importorskip("oracle")
+    oracle.build()
+    shape, h = (10, 12, 8), (0.07, 0.05, 0.09)
+    rho = np.random.default_rng(3).standard_normal(shape)
+    g = oracle.kernel_vgf(list(shape), h)
+    octant = torch.from_numpy(oracle.scaled_spectrum_octant(g, h))
+    phi, E = bench.padded_fft_solve(octant, torch.from_numpy(rho), h)
+    p_ref, E_ref = oracle.solve_with_kernel(g, rho, h)
+    assert np.max(np.abs(phi.numpy() - p_ref)) <= 1e-12 * np.max(np.abs(p_ref))
+    assert np.max(np.abs(torch.stack(E).numpy() - E_ref)) <= 1e-12 * np.max(np.abs(E_ref))
