@@ -249,6 +249,25 @@ def cufft_context(plan, rho, phi, E, steps=20, warmup=3):
             "ms_per_step": ms, "solves_per_s": 1e3 / ms, "max_rel_diff_phi": err_phi, "max_rel_diff_E": err_E}
 
 
+def torch_cpu_context(n=128):
+    """Context only: padded_fft_solve with torch.fft on the host cores (FP32) at n^3,
+    scaled to 256^3 by the N^3 log N work ratio."""
+    import torch
+    prob = W.mixture_3d(n, 8, 1)
+    import oracle
+    g = oracle.kernel_vgf(list(prob.shape), prob.h)
+    octant = torch.from_numpy(oracle.scaled_spectrum_octant(g, prob.h)).to(torch.float32)
+    rho = torch.from_numpy(prob.rho(np.float32))
+    padded_fft_solve(octant, rho, prob.h)
+    t = time.perf_counter()
+    padded_fft_solve(octant, rho, prob.h)
+    t = time.perf_counter() - t
+    scale = (256 ** 3 * math.log2(512 ** 3)) / (n ** 3 * math.log2((2 * n) ** 3))
+    return {"kind": "library context (torch.fft on the host cores, FP32), not the product path",
+            "threads": torch.get_num_threads(), "sample": f"one solve at {n}^3 ({t:.2f} s), scaled by {scale:.2f}",
+            "solves_per_s": 1.0 / (t * scale)}
+
+
 def cpu_model() -> str:
     """The host CPU's name as the kernel reports it (x86 'model name', else the Arm part number)."""
     try:
@@ -459,6 +478,8 @@ def run_gpu(args):
                        "h2d_bytes_per_step": rho.numel() * 4, "d2h_bytes_per_step": (phi.numel() + E.numel()) * 4}
     if ws == 1 and not args.no_context:
         line["context"] = {"cufft": cufft_context(plans["vgf"], rho, phi, E)}
+        if not args.no_cpu_baseline:
+            line["context"]["torch_fft_cpu"] = torch_cpu_context()
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_block()
     print(json.dumps(line), flush=True)
