@@ -175,12 +175,12 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
         const int Ns[3] = {N0, dim == 3 ? N1 : 0, N2};
         for (int a = 0; a < 3 && rc == FSP_OK; ++a)
             if (Ns[a] && cudaMalloc(&p.dtw[a], sizeof(double2) * Ns[a]) != cudaSuccess) rc = FSP_ERR_NOMEM;
-    } else if (cudaMalloc(&p.tw0, sizeof(float2) * (N0 + TW_AUX)) != cudaSuccess) {
+    } else if (cudaMalloc(&p.tw0, sizeof(float2) * twiddle_entries(N0)) != cudaSuccess) {
         rc = FSP_ERR_NOMEM;
     }
     if (rc == FSP_OK && !p.direct) {
         if (dim == 3 && N1 != N0) {
-            if (cudaMalloc(&p.tw1, sizeof(float2) * (N1 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
+            if (cudaMalloc(&p.tw1, sizeof(float2) * twiddle_entries(N1)) != cudaSuccess) rc = FSP_ERR_NOMEM;
         } else {
             p.tw1 = p.tw0;
         }
@@ -188,7 +188,7 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     if (rc == FSP_OK && !p.direct) {
         if (N2 == N0) p.tw2 = p.tw0;
         else if (dim == 3 && N2 == N1) p.tw2 = p.tw1;
-        else if (cudaMalloc(&p.tw2, sizeof(float2) * (N2 + TW_AUX)) != cudaSuccess) rc = FSP_ERR_NOMEM;
+        else if (cudaMalloc(&p.tw2, sizeof(float2) * twiddle_entries(N2)) != cudaSuccess) rc = FSP_ERR_NOMEM;
     }
     p.K_count = (size_t)(p.n[0] + 1) * (p.n[1] + 1) * (dim == 3 ? (p.n[2] + 1) : 1);
     if (rc == FSP_OK && cudaMalloc(&p.K, sizeof(float) * p.K_count) != cudaSuccess) rc = FSP_ERR_NOMEM;
@@ -200,12 +200,12 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
         for (int a = 0; a < 3 && rc == FSP_OK; ++a)
             if (p.dtw[a] && make_direct_twiddles(p.dtw[a], a == 0 ? N0 : a == 1 ? N1 : N2, st)) rc = FSP_ERR_CUDA;
     } else if (rc == FSP_OK) {
-        if (make_twiddles(p.tw0, N0, st) || make_twiddles_aux(p.tw0, N0, st)) rc = FSP_ERR_CUDA;
-        if (rc == FSP_OK && p.tw1 != p.tw0 && (make_twiddles(p.tw1, N1, st) || make_twiddles_aux(p.tw1, N1, st)))
-            rc = FSP_ERR_CUDA;
-        if (rc == FSP_OK && p.tw2 != p.tw0 && p.tw2 != p.tw1 &&
-            (make_twiddles(p.tw2, N2, st) || make_twiddles_aux(p.tw2, N2, st)))
-            rc = FSP_ERR_CUDA;
+        auto fill = [&](float2 *t, int n) {
+            return make_twiddles(t, n, st) || make_twiddles_aux(t, n, st) || make_twiddles_gall(t, n, st);
+        };
+        if (fill(p.tw0, N0)) rc = FSP_ERR_CUDA;
+        if (rc == FSP_OK && p.tw1 != p.tw0 && fill(p.tw1, N1)) rc = FSP_ERR_CUDA;
+        if (rc == FSP_OK && p.tw2 != p.tw0 && p.tw2 != p.tw1 && fill(p.tw2, N2)) rc = FSP_ERR_CUDA;
     }
     if (rc == FSP_OK) rc = build_kernel_spectrum(&p, st);
     if (st) cudaStreamDestroy(st);

@@ -171,6 +171,29 @@ int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int va
     }
 }
 
+// Gathered blocks of every pass (TW_GALL layout) after the N-entry table, for
+// the long-line lengths; count of those entries, 0 for other lengths.
+int twiddle_gall_entries(int N)
+{
+    switch (N) {
+#define X(n) case n: return AuxEndAll<1, 0, typename Plan1D<n>::R>::value;
+        X(1024) X(2048) X(4096) X(8192)
+#undef X
+    default: return 0;
+    }
+}
+
+int make_twiddles_gall(float2 *tw, int N, cudaStream_t st)
+{
+    switch (N) {
+#define X(n) \
+    case n: k_twiddles_gall<n, typename Plan1D<n>::R><<<(n + 255) / 256, 256, 0, st>>>(tw); return (int)cudaGetLastError();
+        X(1024) X(2048) X(4096) X(8192)
+#undef X
+    default: return 0;
+    }
+}
+
 int make_twiddles_aux(float2 *tw, int N, cudaStream_t st)
 {
     switch (N) {

@@ -258,7 +258,10 @@ enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // TW_QSMEM: a shared-memory copy of the first quarter of the table only
 // (N a multiple of 4): W^(m + N/4) = -i W^m, so W^m is the entry m mod N/4
 // turned by (-i)^(m div N/4).
-enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4, TW_QSMEM = 5 };
+// TW_GALL: gathered blocks [r][k] for every pass with NS > 1 (not only NS < 32),
+// read from global memory: a warp's 16-32 consecutive k read consecutive
+// entries (the long-line passes, whose tables do not fit in shared memory).
+enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4, TW_QSMEM = 5, TW_GALL = 7 };
 
 // W_N^m (m < N) from the quarter table.
 template <int N>
@@ -333,13 +336,25 @@ template <int NS, int R, int OFF>
 struct NextOff {
     static constexpr int value = OFF + ((NS > 1 && NS < 32) ? R * NS : 0);
 };
+// The same in the TW_GALL layout (a block for every pass with NS > 1).
+template <int NS, int R, int OFF>
+struct NextOffAll {
+    static constexpr int value = OFF + (NS > 1 ? R * NS : 0);
+};
+template <int TW, int NS, int R, int OFF>
+struct NextOffT {
+    static constexpr int value = TW == TW_GALL ? NextOffAll<NS, R, OFF>::value : NextOff<NS, R, OFF>::value;
+};
 
 // Twiddles of butterfly column k (= b mod NS) in a pass with (NS, R); OFF is
 // the pass's gathered block in the TW_GATHER / TW_SMEM layouts.
 template <int N, int R, bool INV, int NS, int TW, int OFF>
 __device__ __forceinline__ void pass_twiddles(float2 *u, const float2 *__restrict__ tw, int k)
 {
-    if constexpr (TW == TW_QSMEM) {
+    if constexpr (TW == TW_GALL) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + N + OFF + r * NS + k));
+    } else if constexpr (TW == TW_QSMEM) {
         static_assert(N % 4 == 0, "the quarter table needs N divisible by 4");
         const int m = k * (N / (NS * R));
 #pragma unroll
@@ -445,7 +460,7 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
                 }
             }
             lsync<SYNC>();
-            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOff<NS, R, OFF>::value>::template run<false>(v, j, tw,
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOffT<TW, NS, R, OFF>::value>::template run<false>(v, j, tw,
                                                                                                          sm);
             return;
         }
@@ -457,7 +472,7 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
             pass_twiddles<N, R, INV, NS, TW, OFF>(u, tw, k);
             dft<R, INV>(u);
             pair_exchange<E>(v, u, j);
-            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOff<NS, R, OFF>::value>::template run<false>(v, j, tw,
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOffT<TW, NS, R, OFF>::value>::template run<false>(v, j, tw,
                                                                                                          sm);
             return;
         }
@@ -485,7 +500,7 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = sm.at(j + r * T);
             lsync<SYNC>();
-            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOff<NS, R, OFF>::value>::template run<false>(v, j, tw,
+            Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOffT<TW, NS, R, OFF>::value>::template run<false>(v, j, tw,
                                                                                                          sm);
         }
     }
@@ -522,6 +537,44 @@ struct AuxFill<N, NS, OFF, Radices<R, RS...>> {
         AuxFill<N, NS * R, NextOff<NS, R, OFF>::value, Radices<RS...>>::run(aux, i);
     }
 };
+// The TW_GALL layout: a block [r][k] for every pass with NS > 1.
+template <int N, int NS, int OFF, class RAD>
+struct AuxFillAll {
+    static __device__ void run(float2 *, int) {}
+};
+template <int N, int NS, int OFF, int R, int... RS>
+struct AuxFillAll<N, NS, OFF, Radices<R, RS...>> {
+    static __device__ void run(float2 *aux, int i)
+    {
+        if constexpr (NS > 1) {
+            if (i < R * NS) {
+                const int r = i / NS, k = i % NS;
+                const long long e = (long long)r * k * (N / (NS * R));
+                double sn, cs;
+                sincospi(2.0 * (double)(e % N) / (double)N, &sn, &cs);
+                aux[OFF + i] = make_float2((float)cs, (float)-sn);
+            }
+        }
+        AuxFillAll<N, NS * R, NextOffAll<NS, R, OFF>::value, Radices<RS...>>::run(aux, i);
+    }
+};
+template <int NS, int OFF, class RAD>
+struct AuxEndAll;
+template <int NS, int OFF>
+struct AuxEndAll<NS, OFF, Radices<>> {
+    static constexpr int value = OFF;
+};
+template <int NS, int OFF, int R, int... RS>
+struct AuxEndAll<NS, OFF, Radices<R, RS...>> {
+    static constexpr int value = AuxEndAll<NS * R, NextOffAll<NS, R, OFF>::value, Radices<RS...>>::value;
+};
+template <int N, class RAD>
+__global__ void k_twiddles_gall(float2 *tw)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        AuxFillAll<N, 1, 0, RAD>::run(tw + N, i);
+}
+
 template <int N, class RAD>
 __global__ void k_twiddles_aux(float2 *tw)
 {

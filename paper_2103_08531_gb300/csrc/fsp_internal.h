@@ -42,8 +42,15 @@ struct Plan {
 
 // fsp_precompute.cu
 int make_twiddles(float2 *tw, int N, cudaStream_t st);
-int make_twiddles_aux(float2 *tw, int N, cudaStream_t st);   // fsp_axis2.cu
-constexpr int TW_AUX = 1024;   // gathered-twiddle entries after each N-entry table
+int make_twiddles_aux(float2 *tw, int N, cudaStream_t st);    // fsp_axis2.cu
+int make_twiddles_gall(float2 *tw, int N, cudaStream_t st);   // fsp_axis2.cu
+int twiddle_gall_entries(int N);                              // fsp_axis2.cu
+constexpr int TW_AUX = 1024;   // gathered-twiddle entries after each N-entry table (N <= 512)
+inline size_t twiddle_entries(int N)
+{
+    const int g = twiddle_gall_entries(N);
+    return (size_t)N + (size_t)(g > TW_AUX ? g : TW_AUX);
+}
 int build_kernel_spectrum(Plan *p, cudaStream_t st);
 
 // pass kinds

@@ -139,11 +139,15 @@ struct ColCfg {
     }
 };
 
-// Twiddle source of the long-line forward middle pass (TW_POW: 4 table loads
-// and products per radix-16 butterfly, fewer live registers than TW_TABLE).
+// Twiddle source of the long-line forward middle pass, per length as measured:
+// the all-pass gathered table (a warp's consecutive k read consecutive entries)
+// at 2n = 2048 and 8192, power products (TW_POW) at 1024 and 4096, where the
+// gathered loads were slower.  A value here forces one source.
 #ifndef FSP_ROW_TW
-#define FSP_ROW_TW TW_POW
+#define FSP_ROW_TW -1
 #endif
+template <int N>
+constexpr int kRowTw = FSP_ROW_TW >= 0 ? FSP_ROW_TW : ((N == 2048 || N == 8192) ? TW_GALL : TW_POW);
 
 template <int N>
 struct RowCfg {
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
         __syncthreads();
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_BLOCK, kRowTw<N>>(v, j, a.tw2, sm);
         const float *Kr = krow(a, kx, row);
         if constexpr (C::SAVE) {
             float2 *sv = stage + LPC * NH + li * N;   // product spectrum of this line
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
                 v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
                 sv[k] = v[r];
             }
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, kRowTw<N>>(v, j, a.tw2, sm);
             if (act) {
                 float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
                     const float2 sk = sv[k];
                     v[r] = make_float2(kk * sk.y, -kk * sk.x);   // -i k2 (K rho^)
                 }
-                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
+                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, kRowTw<N>>(v, j, a.tw2, sm);
                 if (act) {
                     float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
@@ -457,14 +461,14 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) p3_fwd_blk(const __grid_co
                 const float kk = wave(k, n2, a.k2s);
                 q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
             }
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(v, j, a.tw2, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, kRowTw<N>>(v, j, a.tw2, sm);
             if (act) {
                 float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
                 for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
             }
             if (withE) {
-                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, FSP_ROW_TW>(q, j, a.tw2, sm);
+                line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_BLOCK, kRowTw<N>>(q, j, a.tw2, sm);
                 if (act) {
                     float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
@@ -663,11 +667,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
 // current group is transformed, so the (narrow, row-strided) loads overlap
 // the FFT instead of stalling it.  Layout: exchange buffer (ColCfg), then the
 // stage [rows][BZ] on a 16-byte boundary.
-// Twiddle source of the staged long-column passes: TW_QSMEM (quarter table in
-// shared memory), TW_POW or TW_TABLE.
+// Twiddle source of the staged long-column passes: by default the all-pass
+// gathered table at 2n = 8192 and power products below (measured: the gathered
+// loads win at 4096^2 and lose at 1024^2); a value here forces one source.
 #ifndef FSP_COL_TW
-#define FSP_COL_TW TW_POW
+#define FSP_COL_TW -1
 #endif
+template <int N>
+constexpr int kColTw = FSP_COL_TW >= 0 ? FSP_COL_TW : (N >= 8192 ? TW_GALL : TW_POW);
 
 template <int N>
 struct LongStage {
@@ -736,7 +743,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_co
         __syncthreads();
         if (w + (int)gridDim.x < nw) issue(w + gridDim.x);
         cp_async_commit();
-        line_fft<N, E, false, true, RAD, typename C::View, SYNC_BLOCK, FSP_COL_TW>(v, j, tw, sm);
+        line_fft<N, E, false, true, RAD, typename C::View, SYNC_BLOCK, kColTw<N>>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
         __syncthreads();
@@ -816,7 +823,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_co
         const int tn = next(t + 1);
         if (tn >= 0) issue(tn);
         cp_async_commit();
-        line_fft<N, E, true, false, RAD, typename C::View, SYNC_BLOCK, FSP_COL_TW>(v, j, tw, sm);
+        line_fft<N, E, true, false, RAD, typename C::View, SYNC_BLOCK, kColTw<N>>(v, j, tw, sm);
 #pragma unroll
         for (int r = 0; r < E / 2; ++r) {
             const size_t g = gidx(a, j + r * T, 0, z);
