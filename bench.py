@@ -80,6 +80,33 @@ def pass_bytes(shape, with_E=True):
     }
 
 
+def compulsory_bytes(shape, with_E=True):
+    """Bytes no implementation can avoid: read rho and the kernel octant once, write the outputs once."""
+    cells = int(np.prod(shape))
+    outs = 1 + len(shape) if with_E else 1
+    return 4 * cells + 4 * int(np.prod([n + 1 for n in shape])) + 4 * outs * cells
+
+
+def pipeline_flops(shape, with_E=True):
+    """FP32 flops of the transforms, by the usual count: 5 L log2 L per complex line of length L,
+    half that per real line, padded lengths, pruning ignored. 3D: R2C along axis 0 (n1 n2 real lines),
+    forward along axis 1 (H n2 lines, H = n0+1), along axis 2 (H 2n1 lines: one forward, one inverse
+    per stream), inverse along axis 1 (H n2 lines per output stream), one C2R per real output.
+    2D: R2C, the fused pass (forward plus one inverse per stream), one C2R per real output."""
+    def c(L):
+        return 5 * L * math.log2(L)
+    if len(shape) == 3:
+        n0, n1, n2 = shape
+        H = n0 + 1
+        s3, s4, outs = (2, 3, 4) if with_E else (1, 1, 1)
+        return (n1 * n2 * c(2 * n0) / 2 + H * n2 * c(2 * n1) + (1 + s3) * H * 2 * n1 * c(2 * n2)
+                + s4 * H * n2 * c(2 * n1) + outs * n1 * n2 * c(2 * n0) / 2)
+    n0, n2 = shape
+    H = n0 + 1
+    s3, outs = (2, 3) if with_E else (1, 1)
+    return n2 * c(2 * n0) / 2 + (1 + s3) * H * c(2 * n2) + outs * n2 * c(2 * n0) / 2
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_08531_gb300", "csrc")
@@ -466,6 +493,8 @@ def run_gpu(args):
         "per_pass_gbs": {k: pb[k] / (t * 1e-3) / 1e9 for k, t in zip(names, vgf["per_pass_ms"])},
         "pipeline": {"bytes": total_bytes, "gbs": total_bytes / (ms_step * 1e-3) / 1e9,
                      "frac": total_bytes / (ms_step * 1e-3) / 1e9 / peak},
+        "compulsory": secondary_bytes(compulsory_bytes(prob.shape), ms_step, peak),
+        "flops": secondary_flops(pipeline_flops(prob.shape), ms_step),
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(dom_name, "vgf256"),
@@ -498,6 +527,16 @@ def pass_bytes_2d(shape, with_E=True):
     K = 4 * (n0 + 1) * (n2 + 1)
     s3, outs = (2, 3) if with_E else (1, 1)
     return {"p1_fwd": 4 * cells + 8 * S, "p3_fwd": 8 * S + K + s3 * 8 * S, "p5_fwd": s3 * 8 * S + 4 * outs * cells}
+
+
+def secondary_bytes(byts, ms, peak):
+    return {"bytes": byts, "gbs": byts / (ms * 1e-3) / 1e9, "frac": byts / (ms * 1e-3) / 1e9 / peak,
+            "what": "read rho and the kernel octant, write the outputs, once each"}
+
+
+def secondary_flops(flops, ms):
+    return {"per_solve": flops, "tflops": flops / (ms * 1e-3) / 1e12,
+            "count": "5 L log2 L per complex line, half per real line, pruning ignored (FP32 ALU, not tensor)"}
 
 
 def _timed(fn, steps, warmup):
@@ -579,6 +618,8 @@ def run_other(args):
                      "per_pass_gbs": {k: pass_bytes_2d(prob.shape)[k] / (t * 1e-3) / 1e9 for k, t in per_pass.items()},
                      "pipeline": {"bytes": byts, "gbs": byts / (per * 1e-3) / 1e9,
                                   "frac": byts / (per * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
+                     "compulsory": secondary_bytes(compulsory_bytes(prob.shape), per, peak),
+                     "flops": secondary_flops(pipeline_flops(prob.shape), per),
                      "gpu_launches": 3 * args.steps, "clocks": clk})
     elif args.workload == "train128":
         n, B = 128, 8

@@ -81,3 +81,27 @@ def test_padded_fft_context_solve_matches_oracle():
     p_ref, E_ref = oracle.solve_with_kernel(g, rho, h)
     assert np.max(np.abs(phi.numpy() - p_ref)) <= 1e-12 * np.max(np.abs(p_ref))
     assert np.max(np.abs(torch.stack(E).numpy() - E_ref)) <= 1e-12 * np.max(np.abs(E_ref))
+
+
+def test_compulsory_bytes_at_256_cubed():
+    """rho (4 n^3) + the kernel octant (4 x 257^3) + phi and three field components (16 n^3): about 24 n^3."""
+    n = 256
+    assert bench.compulsory_bytes((n, n, n)) == 4 * n ** 3 + 4 * 257 ** 3 + 16 * n ** 3 == 403442692
+    assert bench.compulsory_bytes((n, n, n), False) == 8 * n ** 3 + 4 * 257 ** 3
+    # 2D: rho, the (n+1)^2 kernel quadrant, phi and two field components
+    assert bench.compulsory_bytes((4096, 4096)) == 16 * 4096 ** 2 + 4 * 4097 ** 2
+
+
+def test_pipeline_flops_by_line_count():
+    """At 256^3 every transform has padded length 512 (5 * 512 * 9 = 23040 flops per complex line):
+    65536 real R2C lines, 65792 forward lines along y, 3 x 131584 lines along z (one forward, two
+    inverse streams), 3 x 65792 inverse lines along y, 4 x 65536 real C2R lines; about 1.9e10."""
+    c = 23040
+    want = 65536 * c / 2 + 65792 * c + 3 * 131584 * c + 3 * 65792 * c + 4 * 65536 * c / 2
+    got = bench.pipeline_flops((256, 256, 256))
+    assert got == want == 18933350400
+    # 2D 4096^2: lengths 8192 (5 * 8192 * 13 = 532480): 4096 R2C lines, 3 x 4097 lines in the fused pass,
+    # 3 x 4096 C2R lines
+    c2 = 532480
+    assert bench.pipeline_flops((4096, 4096)) == 4096 * c2 / 2 + 3 * 4097 * c2 + 3 * 4096 * c2 / 2
+    assert bench.pipeline_flops((64, 64, 64), False) < bench.pipeline_flops((64, 64, 64))
