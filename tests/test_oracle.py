@@ -107,6 +107,33 @@ def test_kernel_even_and_spectrum_real(oracle_mod, method):
     assert np.max(np.abs(spec.imag)) < 1e-12 * np.max(np.abs(spec.real))
 
 
+@pytest.mark.parametrize("method", ["he", "vgf"])
+def test_kernel_at_minus_n_never_reaches_phi(oracle_mod, method):
+    """Sec. 2's restriction keeps j_a in [-n_a, n_a); the plane j_a = -n_a (stored at index n_a)
+    is never reached by the cropped convolution phi_i = sum_j rho_j g_(i-j), |i_a - j_a| <= n_a - 1.
+    Changing g there leaves phi alone; a restriction shifted by one index would not. E does feel it:
+    the spectral derivative (Sec. 4) is a dense circulant on the padded grid, so it reads phi~ at the
+    padded points too, and those see the plane."""
+    shape, h = (5, 6, 4), (0.11, 0.09, 0.13)
+    rho = np.random.default_rng(21).standard_normal(shape)
+    g = oracle_mod.kernel(method, list(shape), h)
+    p0, E0 = oracle_mod.solve_with_kernel(g, rho, h)
+    for a, n in enumerate(shape):
+        g2 = g.copy()
+        sl = [slice(None)] * 3
+        sl[a] = n
+        g2[tuple(sl)] += 7.0
+        p1, E1 = oracle_mod.solve_with_kernel(g2, rho, h)
+        assert np.max(np.abs(p1 - p0)) < 1e-12 * np.max(np.abs(p0))
+        assert np.max(np.abs(E1 - E0)) > 1e-3 * np.max(np.abs(E0))
+        # one plane inside the restricted window does reach phi
+        g3 = g.copy()
+        sl[a] = n - 1
+        g3[tuple(sl)] += 7.0
+        p3, _ = oracle_mod.solve_with_kernel(g3, rho, h)
+        assert np.max(np.abs(p3 - p0)) > 1e-3 * np.max(np.abs(p0))
+
+
 def test_vgf_spectrum_at_k0_limits():
     """The k -> 0 values of F{G^L} (3D L^2/2, 2D (L^2/4)(1 - 2 ln L)) match the limit of the formula."""
     from scipy import special
