@@ -18,6 +18,14 @@
 // and K = (1 / prod(2 n_a M_a)) (P_0 x P_1 x P_2) Ghat: three contractions over
 // the oversampled octant instead of an FFT of the whole (M_a)^d grid.  Axes are
 // contracted in order of decreasing shrink ratio (M_a/2+1)/(n_a+1).
+//
+// Each P entry is evaluated in closed form, not as an (n+1)-term sum: with the
+// weights c the j-sum runs over j in [-n, n) (the term at -n equals the one at
+// n), the product of cosines splits into cos((a+b) j) + cos((a-b) j), and
+//     sum_{j=-n}^{n-1} cos(j t) = sin(n t) cot(t / 2)      (2n where t = 0 mod 2 pi).
+// With a = pi k / n and b = 2 pi m / M the angles are pi r / (n M) for the
+// integers r = k M +- 2 m n, so every sine is taken of an argument reduced
+// exactly in integer arithmetic.
 #include "fsp_internal.h"
 
 #include <algorithm>
@@ -77,17 +85,39 @@ __global__ void k_matrix_he(double *Q, int n)
     Q[(size_t)k * (n + 1) + j] = c * cospi_ratio((long long)k * j, n);
 }
 
+// sin(pi a / b) for integers, b > 0: a reduced exactly to [0, b/2] first, so
+// the double argument of sinpi lies in [0, 1/2] and keeps its relative accuracy.
+__device__ __forceinline__ double sinpi_ratio(long long a, long long b)
+{
+    long long r = a % (2 * b);
+    if (r < 0) r += 2 * b;
+    double sgn = 1.0;
+    if (r >= b) {           // sin(pi + x) = -sin(x)
+        r -= b;
+        sgn = -1.0;
+    }
+    if (2 * r > b) r = b - r;   // sin(pi - x) = sin(x)
+    return sgn * sinpi((double)r / (double)b);
+}
+
+// sum_{j=-n}^{n-1} cos(pi r j / (n M)) = sin(pi r / M) cot(pi r / (2 n M)),
+// and 2n where r is a multiple of 2 n M; the cosine of the cotangent is taken
+// as sin(pi (n M - r) / (2 n M)).
+__device__ __forceinline__ double cos_sum_sym(long long r, long long n, long long M)
+{
+    const long long D = n * M;
+    if (r % (2 * D) == 0) return 2.0 * (double)n;
+    return sinpi_ratio(r, M) * sinpi_ratio(D - r, 2 * D) / sinpi_ratio(r, 2 * D);
+}
+
 // P[k][m] = w_m sum_j c_j cos(pi k j / n) cos(2 pi m j / M), k in [0,n], m in [0, M/2]
 __global__ void k_matrix_vgf(double *P, int n, int M)
 {
     int k = blockIdx.y, m = blockIdx.x * blockDim.x + threadIdx.x;
     int mh = M / 2 + 1;
     if (m >= mh || k > n) return;
-    double s = 0.0;
-    for (int j = 0; j <= n; ++j) {
-        double c = (j == 0 || j == n) ? 1.0 : 2.0;
-        s += c * cospi_ratio((long long)k * j, n) * cospi_ratio(2LL * m * j, M);
-    }
+    const long long a = (long long)k * M, b = 2LL * m * n;
+    const double s = 0.5 * (cos_sum_sym(a + b, n, M) + cos_sum_sym(a - b, n, M));
     double w = (m == 0 || 2 * m == M) ? 1.0 : 2.0;
     P[(size_t)k * mh + m] = w * s;
 }
