@@ -656,6 +656,36 @@ def run_other(args):
                      "config": {"workload": "8 x 128^3 VGF, 4-Gaussian densities (seeds 10..17), "
                                             "loss sum (phi - phi_t)^2 + 0.1 |E|^2"},
                      "gpu_launches": None, "clocks": clk})
+    elif args.workload == "fd_direct":
+        # the finite-difference field on a solved 256^3 HE potential, and FP64 direct-path solves at the
+        # odd sizes of the paper's convergence studies
+        prob = W.mixture_3d(256, 8, 1)
+        plan = fsp.Plan(prob.shape, prob.h, "he")
+        phi, _ = plan.solve(torch.from_numpy(prob.rho(np.float32)).cuda(), with_E=False)
+        E = torch.empty((3,) + prob.shape, dtype=torch.float32, device="cuda")
+        clocks.start()
+        per_fd = _timed(lambda: plan.gradient_fd(phi, E), args.steps, args.warmup) / args.steps
+        direct = {}
+        for name, shape, h in (("13x17x11", (13, 17, 11), (0.05, 0.04, 0.06)), ("50x37", (50, 37), (0.02, 0.03))):
+            d = len(shape)
+            dp = fsp.Plan(shape, h, "vgf", dtype="f64")
+            src = W.Problem(name, shape, h, [(np.zeros(d), np.full(d, 0.1), 1.0)])
+            r = torch.from_numpy(src.rho(np.float64)).cuda()
+            po = torch.empty_like(r)
+            Eo = torch.empty((d,) + shape, dtype=torch.float64, device="cuda")
+            direct[name] = _timed(lambda: dp.solve(r, phi=po, E=Eo), args.steps, args.warmup) / args.steps
+        clk = clocks.stop()
+        fd_bytes = 16 * prob.points      # read phi, write three field components (FP32)
+        line.update({"metric": "finite-difference E at 256^3 FP32 (GB/s of phi read + E written)",
+                     "value": fd_bytes / (per_fd * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": per_fd,
+                     "config": {"workload": "E = -grad phi by centred differences on a 256^3 HE potential "
+                                            "(8 anisotropic Gaussians, seed 1); FP64 direct-sum VGF solves",
+                                "l2": "phi 67 MB read + E 201 MB written per step, 268 MB > 129 MB L2, no flush"},
+                     "roofline": {"bound": "hbm", "kernel": "k_fd_gradient", "achieved": fd_bytes / (per_fd * 1e-3) / 1e9,
+                                  "peak": peak, "unit": "GB/s", "frac": fd_bytes / (per_fd * 1e-3) / 1e9 / peak,
+                                  "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes": fd_bytes},
+                     "direct_f64_ms_per_solve": direct,
+                     "gpu_launches": args.steps, "clocks": clk})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -669,7 +699,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-context", action="store_true", help="skip the torch.fft (cuFFT) context timing")
-    ap.add_argument("--workload", choices=["vgf256", "beam64", "gauss2d4096", "train128"], default="vgf256",
+    ap.add_argument("--workload", choices=["vgf256", "beam64", "gauss2d4096", "train128", "fd_direct"], default="vgf256",
                     help="vgf256 is the headline; the others print their own line (1 GPU)")
     args = ap.parse_args()
     if args.warmup < 3:
