@@ -87,8 +87,8 @@ def compulsory_bytes(shape, with_E=True):
     return 4 * cells + 4 * int(np.prod([n + 1 for n in shape])) + 4 * outs * cells
 
 
-def pipeline_flops(shape, with_E=True):
-    """FP32 flops of the transforms, by the usual count: 5 L log2 L per complex line of length L,
+def pass_flops(shape, with_E=True):
+    """FP32 flops of the transforms per pass, by the usual count: 5 L log2 L per complex line of length L,
     half that per real line, padded lengths, pruning ignored. 3D: R2C along axis 0 (n1 n2 real lines),
     forward along axis 1 (H n2 lines, H = n0+1), along axis 2 (H 2n1 lines: one forward, one inverse
     per stream), inverse along axis 1 (H n2 lines per output stream), one C2R per real output.
@@ -99,12 +99,21 @@ def pipeline_flops(shape, with_E=True):
         n0, n1, n2 = shape
         H = n0 + 1
         s3, s4, outs = (2, 3, 4) if with_E else (1, 1, 1)
-        return (n1 * n2 * c(2 * n0) / 2 + H * n2 * c(2 * n1) + (1 + s3) * H * 2 * n1 * c(2 * n2)
-                + s4 * H * n2 * c(2 * n1) + outs * n1 * n2 * c(2 * n0) / 2)
+        return {"p1_fwd": n1 * n2 * c(2 * n0) / 2, "p2_fwd": H * n2 * c(2 * n1),
+                "p3_fwd": (1 + s3) * H * 2 * n1 * c(2 * n2), "p4_fwd": s4 * H * n2 * c(2 * n1),
+                "p5_fwd": outs * n1 * n2 * c(2 * n0) / 2}
     n0, n2 = shape
     H = n0 + 1
     s3, outs = (2, 3) if with_E else (1, 1)
-    return n2 * c(2 * n0) / 2 + (1 + s3) * H * c(2 * n2) + outs * n2 * c(2 * n0) / 2
+    return {"p1_fwd": n2 * c(2 * n0) / 2, "p3_fwd": (1 + s3) * H * c(2 * n2), "p5_fwd": outs * n2 * c(2 * n0) / 2}
+
+
+def pipeline_flops(shape, with_E=True):
+    return sum(pass_flops(shape, with_E).values())
+
+
+# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def kernel_source_hash():
@@ -506,6 +515,7 @@ def run_gpu(args):
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(dom_name, "vgf256"),
                      "algorithmic_bytes": pb[dom_name]},
+        "alu_check": alu_check(dom_name, pass_flops(prob.shape)[dom_name], vgf["per_pass_ms"][dom]),
         "gpu_launches": npass * args.steps,
         "clocks": clk,
     }
@@ -544,6 +554,13 @@ def secondary_bytes(byts, ms, peak):
 def secondary_flops(flops, ms):
     return {"per_solve": flops, "tflops": flops / (ms * 1e-3) / 1e12,
             "count": "5 L log2 L per complex line, half per real line, pruning ignored (FP32 ALU, not tensor)"}
+
+
+def alu_check(kernel, flops, ms):
+    """The dominant kernel's transform arithmetic against the FP32 ALU peak (a secondary roofline)."""
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"kernel": kernel, "flops": flops, "tflops": tf, "peak_tflops": FP32_PEAK_TFLOPS, "frac": tf / FP32_PEAK_TFLOPS,
+            "peak_from": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz; flops by 5 L log2 L per line"}
 
 
 def _timed(fn, steps, warmup):

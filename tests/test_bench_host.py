@@ -105,3 +105,17 @@ def test_pipeline_flops_by_line_count():
     c2 = 532480
     assert bench.pipeline_flops((4096, 4096)) == 4096 * c2 / 2 + 3 * 4097 * c2 + 3 * 4096 * c2 / 2
     assert bench.pipeline_flops((64, 64, 64), False) < bench.pipeline_flops((64, 64, 64))
+
+
+def test_pass_flops_split_and_alu_peak():
+    """Per-pass flops sum to the pipeline count; the middle pass carries three of the 512-point
+    transforms per line (9.1e9 at 256^3); the FP32 peak is 152 x 128 x 2 x 2.07 GHz."""
+    f = bench.pass_flops((256, 256, 256))
+    assert set(f) == set(bench.pass_bytes((256, 256, 256)))
+    assert sum(f.values()) == bench.pipeline_flops((256, 256, 256))
+    assert f["p3_fwd"] == 3 * 257 * 512 * 23040
+    assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
+    a = bench.alu_check("p3_fwd", f["p3_fwd"], 0.25)
+    assert abs(a["tflops"] - f["p3_fwd"] / 0.25e-3 / 1e12) < 1e-9 and 0 < a["frac"] < 1
+    f2 = bench.pass_flops((4096, 4096))
+    assert set(f2) == set(bench.pass_bytes_2d((4096, 4096))) and sum(f2.values()) == bench.pipeline_flops((4096, 4096))
