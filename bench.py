@@ -112,8 +112,14 @@ def pipeline_flops(shape, with_E=True):
     return sum(pass_flops(shape, with_E).values())
 
 
-# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+def fp32_peak_tflops(sms, sm_mhz):
+    """FP32 ALU peak from unit counts and clock: SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def device_sms(device=0):
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
 
 
 def kernel_source_hash():
@@ -515,7 +521,8 @@ def run_gpu(args):
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(dom_name, "vgf256"),
                      "algorithmic_bytes": pb[dom_name]},
-        "alu_check": alu_check(dom_name, pass_flops(prob.shape)[dom_name], vgf["per_pass_ms"][dom]),
+        "alu_check": alu_check(dom_name, pass_flops(prob.shape)[dom_name], vgf["per_pass_ms"][dom],
+                               device_sms(local), *alu_clock(clk)),
         "gpu_launches": npass * args.steps,
         "clocks": clk,
     }
@@ -556,11 +563,23 @@ def secondary_flops(flops, ms):
             "count": "5 L log2 L per complex line, half per real line, pruning ignored (FP32 ALU, not tensor)"}
 
 
-def alu_check(kernel, flops, ms):
-    """The dominant kernel's transform arithmetic against the FP32 ALU peak (a secondary roofline)."""
+def alu_check(kernel, flops, ms, sms, sm_mhz, clock_from):
+    """The dominant kernel's transform arithmetic against the FP32 ALU peak (a secondary roofline):
+    the peak counts this device's SMs at the SM clock sampled while the kernel ran."""
     tf = flops / (ms * 1e-3) / 1e12
-    return {"kernel": kernel, "flops": flops, "tflops": tf, "peak_tflops": FP32_PEAK_TFLOPS, "frac": tf / FP32_PEAK_TFLOPS,
-            "peak_from": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz; flops by 5 L log2 L per line"}
+    peak = fp32_peak_tflops(sms, sm_mhz)
+    return {"kernel": kernel, "flops": flops, "tflops": tf, "peak_tflops": peak, "frac": tf / peak,
+            "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz ({clock_from}); "
+                         "flops by 5 L log2 L per line"}
+
+
+def alu_clock(clk):
+    """SM clock for the ALU peak: the median sampled under load, else the reported maximum, else 2070 MHz."""
+    if clk and clk.get("sm_mhz"):
+        return float(clk["sm_mhz"]), "median SM clock sampled in the timed region"
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"]), "maximum SM clock reported by nvidia-smi"
+    return 2070.0, "nominal maximum SM clock (no clock samples)"
 
 
 def _timed(fn, steps, warmup):

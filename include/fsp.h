@@ -112,10 +112,21 @@ const char *fsp_error_string(int status);
  */
 int fsp_plan_geometry(const fsp_plan *plan, int *dim, int *n, double *h, double *L, int *M);
 
-/* Device workspace one solve (or adjoint) needs, in bytes; batch >= 1 multiplies it. */
+/*
+ * Device workspace one solve needs, in bytes; batch >= 1 multiplies it.
+ * with_E = 0 sizes it for solves without E (and adjoints without g_E): a 2D
+ * FFT-path plan then needs one intermediate buffer instead of two; 3D and
+ * direct-sum plans need the same either way.  Returns 0 for a NULL plan or
+ * batch < 1.
+ */
 size_t fsp_plan_workspace_bytes(const fsp_plan *plan, int with_E, int batch);
 
-/* Hand the plan a device workspace (the caller keeps ownership). */
+/*
+ * Hand the plan a device workspace (the caller keeps ownership; 256-byte
+ * aligned, else FSP_ERR_INVALID).  bytes below fsp_plan_workspace_bytes(plan,
+ * 0, 1) is FSP_ERR_WORKSPACE; each solve checks the size it needs for its own
+ * outputs and returns FSP_ERR_WORKSPACE if the workspace is smaller.
+ */
 int fsp_plan_set_workspace(fsp_plan *plan, void *dev_ptr, size_t bytes);
 
 /*
@@ -214,12 +225,16 @@ void fsp_plan_destroy(fsp_plan *plan);
  * geometry).  A grid whose workspace (fsp_plan_workspace_bytes) exceeds the
  * scratch returns FSP_ERR_WORKSPACE (3D cubes up to 128^3 fit).
  *
- * The first call on a device looks up the scratch address on that device
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Set-up: the first call on a device, with that device current, looks up
+ * the scratch address on that device (cudaGetSymbolAddress) and keeps it;
+ * make that first call before any stream capture.  The address belongs to the
+ * device's CUDA context: after cudaDeviceReset the next call looks it up
+ * again, so after a reset, too, call once outside any capture first.
  * Every call on a device shares the one scratch array and it keeps the last
  * call's contents (each solve writes every scratch element it later reads, so
  * nothing needs clearing).  Calls that overlap on the GPU (different streams,
- * or different plans at once) race on the scratch: serialise them.
+ * or different plans at once) race on the scratch: serialise them.  The
+ * status is also left in fsp_last_error(), as for every other entry point.
  */
 #define FSP_NOALLOC_SCRATCH_BYTES (80u * 1024u * 1024u)
 int fsp_solve_noalloc(fsp_plan *plan, const void *rho, void *phi, void *E, void *cuda_stream);

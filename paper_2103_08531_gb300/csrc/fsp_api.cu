@@ -21,6 +21,8 @@ static int set_err(int e)
     return e;
 }
 
+int fsp::record_error(int s) { return set_err(s); }
+
 extern "C" int fsp_last_error(void) { return g_last_error; }
 
 extern "C" const char *fsp_error_string(int s)
@@ -248,22 +250,26 @@ extern "C" int fsp_plan_geometry(const fsp_plan *plan, int *dim, int *n, double 
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static size_t per_solve_bytes(const Plan &p)
+// Workspace of one solve: the two intermediate buffers (buf0, buf1) of the
+// FFT passes, or the direct-sum path's regions.  A 2D solve without E (and a
+// 2D adjoint without g_E) never touches buf1; in 3D the first pass writes
+// buf1 whatever the outputs.
+static size_t per_solve_bytes(const Plan &p, bool with_E)
 {
-    return p.direct ? direct_workspace_bytes(p) : 2 * align_up(p.buf_elems * sizeof(float2), 256);
+    if (p.direct) return direct_workspace_bytes(p);
+    return (p.three_d || with_E ? 2 : 1) * align_up(p.buf_elems * sizeof(float2), 256);
 }
 
 extern "C" size_t fsp_plan_workspace_bytes(const fsp_plan *plan, int with_E, int batch)
 {
-    (void)with_E;
     if (!plan || batch < 1) return 0;
-    return per_solve_bytes(plan->p) * (size_t)batch;
+    return per_solve_bytes(plan->p, with_E != 0) * (size_t)batch;
 }
 
 extern "C" int fsp_plan_set_workspace(fsp_plan *plan, void *dev_ptr, size_t bytes)
 {
     if (!plan || !dev_ptr || ((uintptr_t)dev_ptr % 256) != 0) return set_err(FSP_ERR_INVALID);
-    if (bytes < per_solve_bytes(plan->p)) return set_err(FSP_ERR_WORKSPACE);
+    if (bytes < per_solve_bytes(plan->p, false)) return set_err(FSP_ERR_WORKSPACE);
     plan->p.ws = dev_ptr;
     plan->p.ws_bytes = bytes;
     return set_err(FSP_OK);
@@ -467,7 +473,7 @@ extern "C" int fsp_solve(fsp_plan *plan, const void *rho, void *phi, void *E, vo
     if (!plan || !rho || (!phi && !E)) return set_err(FSP_ERR_INVALID);
     if (!aligned16(rho) || (phi && !aligned16(phi)) || (E && !aligned16(E))) return set_err(FSP_ERR_INVALID);
     const Plan &p = plan->p;
-    if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return set_err(FSP_ERR_WORKSPACE);
+    if (!p.ws || p.ws_bytes < per_solve_bytes(p, E != nullptr)) return set_err(FSP_ERR_WORKSPACE);
     return set_err(run_forward(p, p.ws, (const float *)rho, (float *)phi, (float *)E, (cudaStream_t)cuda_stream));
 }
 
@@ -476,7 +482,7 @@ extern "C" int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *
     if (!plan || !g_rho || (!g_phi && !g_E)) return set_err(FSP_ERR_INVALID);
     if ((g_phi && !aligned16(g_phi)) || (g_E && !aligned16(g_E)) || !aligned16(g_rho)) return set_err(FSP_ERR_INVALID);
     const Plan &p = plan->p;
-    if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return set_err(FSP_ERR_WORKSPACE);
+    if (!p.ws || p.ws_bytes < per_solve_bytes(p, g_E != nullptr)) return set_err(FSP_ERR_WORKSPACE);
     return set_err(run_adjoint(p, p.ws, (const float *)g_phi, (const float *)g_E, (float *)g_rho,
                                (cudaStream_t)cuda_stream));
 }
@@ -504,7 +510,7 @@ static int check_batch(fsp_plan *const *plans, int count, const void *const *rho
         if (E && !E[i]) return FSP_ERR_INVALID;   // with_E must hold for every item
         if ((phi && phi[i] && !aligned16(phi[i])) || (E && E[i] && !aligned16(E[i]))) return FSP_ERR_INVALID;
         const Plan &p = plans[i]->p;
-        if (!p.ws || p.ws_bytes < per_solve_bytes(p)) return FSP_ERR_WORKSPACE;
+        if (!p.ws || p.ws_bytes < per_solve_bytes(p, E != nullptr)) return FSP_ERR_WORKSPACE;
         for (int k = 0; k < i; ++k)
             if (plans[k] == plans[i]) return FSP_ERR_INVALID;
     }

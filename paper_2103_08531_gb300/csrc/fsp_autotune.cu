@@ -123,7 +123,14 @@ int tuned_variant(int kind, int N)
 // 1: read it and time the passes it lacks; 2: time every pass of the plan.
 // The timing solves run on a private stream with scratch buffers allocated
 // here (this call allocates; solves never do).
+static int autotune(fsp_plan *plan, const char *cache_path, int mode);
+
 extern "C" int fsp_autotune(fsp_plan *plan, const char *cache_path, int mode)
+{
+    return record_error(autotune(plan, cache_path, mode));
+}
+
+static int autotune(fsp_plan *plan, const char *cache_path, int mode)
 {
     if (!plan || mode < 0 || mode > 2) return FSP_ERR_INVALID;
     const Plan &p = plan->p;

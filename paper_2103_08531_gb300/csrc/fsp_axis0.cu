@@ -1,6 +1,6 @@
 // fsp_axis0.cu -- launchers of the axis-0 passes (P1 real -> half spectrum, P5 back).
 #include "fsp_internal.h"
-#include "fsp_passes.cuh"
+#include "fsp_launch.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -8,51 +8,6 @@
 namespace fsp {
 
 #define FSP_AXIS0_SIZES(X) X(64) X(128) X(192) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
-
-namespace {
-
-template <int MAXI>
-Work<MAXI> make_work(const PassArgs *items, int n, int (*units)(const PassArgs &))
-{
-    Work<MAXI> w;
-    w.nitems = n;
-    w.offs[0] = 0;
-    for (int i = 0; i < n; ++i) {
-        w.item[i] = items[i];
-        w.offs[i + 1] = w.offs[i] + units(items[i]);
-    }
-    return w;
-}
-
-int sm_count()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    return sms;
-}
-
-// Launch helper: runs `body(work, grid_cap)` over items in chunks of BATCH_MAX.
-template <class F>
-int chunked(const PassArgs *items, int n, int (*units)(const PassArgs &), F body)
-{
-    if (n == 1) {
-        Work<1> w = make_work<1>(items, 1, units);
-        return body(w);
-    }
-    for (int i = 0; i < n; i += BATCH_MAX) {
-        const int m = std::min(BATCH_MAX, n - i);
-        Work<BATCH_MAX> w = make_work<BATCH_MAX>(items + i, m, units);
-        int e = body(w);
-        if (e) return e;
-    }
-    return 0;
-}
-
-} // namespace
 
 int supported_axis0(int N)
 {

@@ -78,6 +78,13 @@ int run_direct_forward(const Plan &p, void *ws, const void *rho, void *phi, void
 int run_direct_adjoint(const Plan &p, void *ws, const void *g_phi, const void *g_E, void *g_rho, cudaStream_t st);
 int make_direct_twiddles(double2 *tw, int N, cudaStream_t st);   // fsp_precompute.cu
 
+// fsp_api.cu: the forward and adjoint pipelines of one plan on workspace ws
+int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st);
+int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, float *g_rho, cudaStream_t st);
+// Store status s as the calling thread's fsp_last_error() and return it; every
+// C entry point returns through this.
+int record_error(int s);
+
 // fsp_autotune.cu: the variant chosen for a pass kind at padded length N (0 if untuned)
 int tuned_variant(int kind, int N);
 constexpr int PASS_KINDS = 8;

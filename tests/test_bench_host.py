@@ -109,13 +109,17 @@ def test_pipeline_flops_by_line_count():
 
 def test_pass_flops_split_and_alu_peak():
     """Per-pass flops sum to the pipeline count; the middle pass carries three of the 512-point
-    transforms per line (9.1e9 at 256^3); the FP32 peak is 152 x 128 x 2 x 2.07 GHz."""
+    transforms per line (9.1e9 at 256^3); the FP32 peak is SMs x 128 x 2 x clock (152 SMs at 2.07 GHz:
+    80.5 TFLOP/s), with the clock taken from the samples when there are any."""
     f = bench.pass_flops((256, 256, 256))
     assert set(f) == set(bench.pass_bytes((256, 256, 256)))
     assert sum(f.values()) == bench.pipeline_flops((256, 256, 256))
     assert f["p3_fwd"] == 3 * 257 * 512 * 23040
-    assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
-    a = bench.alu_check("p3_fwd", f["p3_fwd"], 0.25)
+    assert abs(bench.fp32_peak_tflops(152, 2070) - 80.54784) < 1e-9
+    a = bench.alu_check("p3_fwd", f["p3_fwd"], 0.25, 152, 2070.0, "test")
     assert abs(a["tflops"] - f["p3_fwd"] / 0.25e-3 / 1e12) < 1e-9 and 0 < a["frac"] < 1
+    assert abs(a["peak_tflops"] - 80.54784) < 1e-9
+    assert bench.alu_clock({"sm_mhz": 1800.0, "sm_max_mhz": 2070.0})[0] == 1800.0
+    assert bench.alu_clock(None)[0] == 2070.0
     f2 = bench.pass_flops((4096, 4096))
     assert set(f2) == set(bench.pass_bytes_2d((4096, 4096))) and sum(f2.values()) == bench.pipeline_flops((4096, 4096))

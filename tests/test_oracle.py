@@ -164,6 +164,23 @@ def test_c1_cube_closed_form(oracle_mod):
     assert 1e-3 < hp < 1e-1 and hE > 1e-3
 
 
+def test_he_g0_enters_as_a_point_self_term(oracle_mod):
+    """HE replaces G(0) by a finite value (paper Sec. 1: 1 in 3D; Sec. 3.1: 1/(2 pi) in 2D).  The
+    solve is linear in the kernel and that value sits at offset 0 only, so changing it moves phi by
+    (g0 - g0') prod(h) rho at every cell and nowhere else: the literal defaults must show up there
+    with exactly those constants."""
+    rng = np.random.default_rng(31)
+    for n, h, g0 in (((10, 12, 9), (0.1, 0.07, 0.12), 1.0), ((14, 11), (0.09, 0.13), 1.0 / (2.0 * math.pi))):
+        rho = rng.standard_normal(n)
+        phi_def, _ = oracle_mod.solve_with_kernel(oracle_mod.kernel_he(list(n), h), rho, h, with_E=False)
+        phi_zero, _ = oracle_mod.solve_with_kernel(oracle_mod.kernel_he(list(n), h, g0=0.0), rho, h, with_E=False)
+        want = g0 * float(np.prod(h)) * rho
+        assert np.max(np.abs((phi_def - phi_zero) - want)) <= 1e-12 * np.max(np.abs(want))
+        # the same through the method name the GPU path uses
+        phi_m, _ = oracle_mod.solve("he", rho, h, with_E=False)
+        assert np.max(np.abs(phi_m - phi_def)) <= 1e-13 * np.max(np.abs(phi_def))
+
+
 def test_paper_3d_example(oracle_mod):
     """Paper Sec. 3, 3D: sigma = 0.05 on [-0.5,0.5]^3; VGF far below HE at N = 32, 64."""
     for n, vgf_tol in ((32, 1e-7), (64, 1e-13)):
