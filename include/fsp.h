@@ -201,6 +201,35 @@ int fsp_autotune(fsp_plan *plan, const char *cache_path, int mode);
 int fsp_tuned_variant(int kind, int N);
 
 /*
+ * Host-resident grids.  A pipe owns `depth` device buffer sets (rho, and phi
+ * and/or E as chosen at creation) and three CUDA streams: copy-in,
+ * compute and copy-out.  fsp_host_pipe_solve enqueues `count` solves of host
+ * grids rho_host[i] -> phi_host[i], E_host[i] (layouts as for fsp_solve, in
+ * the plan's precision) through slot i % depth: the copy of rho in, the
+ * solve (the plan's passes on the plan's workspace), the copy of the outputs
+ * out; the transfers of one solve overlap the kernels of its neighbours.  It
+ * returns once everything is queued (asynchronous): the copies start after
+ * the work already queued on cuda_stream, and cuda_stream waits for the last
+ * copy-out, so an event recorded on cuda_stream after the call, or a
+ * synchronisation of it, covers every copy and solve.  Host buffers should be
+ * page-locked (cudaMallocHost / cudaHostRegister) for the copies to overlap;
+ * pageable buffers still give correct results.  They must stay valid until
+ * cuda_stream has passed the call.  phi_host (E_host) must be non-NULL,
+ * with non-NULL entries, exactly when the pipe was created with with_phi
+ * (with_E).  The plan needs its workspace set (FSP_ERR_WORKSPACE otherwise)
+ * and must not run other solves while the pipe works.  fsp_host_pipe_create
+ * allocates (set-up); fsp_host_pipe_solve does not.  depth: 1 .. 8.
+ * fsp_host_pipe_destroy waits for the pipe's streams, then frees it.
+ * Not part of the paper's method: it is how a caller with host data reaches
+ * the solver end to end.
+ */
+typedef struct fsp_host_pipe fsp_host_pipe;
+fsp_host_pipe *fsp_host_pipe_create(fsp_plan *plan, int depth, int with_phi, int with_E);
+int fsp_host_pipe_solve(fsp_host_pipe *pipe, int count, const void *const *rho_host, void *const *phi_host,
+                        void *const *E_host, void *cuda_stream);
+void fsp_host_pipe_destroy(fsp_host_pipe *pipe);
+
+/*
  * Test hook: copy the plan's FP32 kernel spectrum to host memory, layout
  * [nx+1][ny+1][nz+1] (2D: [nx+1][ny+1]), entry (kx,ky,kz) = prod(h)/prod(2n)
  * times the DFT of the padded kernel at index k (indices k and 2n-k share it).

@@ -42,6 +42,9 @@ SIGNATURES = {
     "fsp_plan_kernel_spectrum": (_i, [_vp, _vp, _sz]),
     "fsp_plan_destroy": (None, [_vp]),
     "fsp_solve_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fsp_host_pipe_create": (_vp, [_vp, _i, _i, _i]),
+    "fsp_host_pipe_solve": (_i, [_vp, _i, _vpp, _vpp, _vpp, _vp]),
+    "fsp_host_pipe_destroy": (None, [_vp]),
 }
 
 

@@ -247,51 +247,65 @@ class Batch:
 
 
 class HostPipeline:
-    """Solves host-resident densities with copies overlapped on three streams.
+    """Solves host-resident densities through the C ABI's host pipe (fsp_host_pipe_*).
 
-    Slot i of `depth` device buffer sets goes host->device on the copy-in
-    stream, is solved on the compute stream (the plan's workspace serialises
-    solves there), and returns device->host on the copy-out stream, so the
-    transfers of neighbouring solves run under each other's kernels.  Host
-    buffers should be pinned (torch.Tensor.pin_memory()) for the copies to be
-    asynchronous.
+    The library owns `depth` device buffer sets and three streams (copy-in,
+    compute, copy-out): slot i % depth is copied in, solved on the plan's
+    workspace, and copied back, so the transfers of neighbouring solves run
+    under each other's kernels.  Host tensors should be pinned
+    (torch.Tensor.pin_memory()) for the copies to overlap.
     """
 
     def __init__(self, plan: Plan, depth: int = 2, with_phi: bool = True, with_E: bool = True):
+        self.lib = _lib.load()
         self.plan, self.depth, self.with_phi, self.with_E = plan, depth, with_phi, with_E
-        dev = plan.device
-        self.rho = [torch.empty(plan.shape, dtype=plan.dtype, device=dev) for _ in range(depth)]
-        self.phi = [torch.empty(plan.shape, dtype=plan.dtype, device=dev) if with_phi else None
-                    for _ in range(depth)]
-        self.E = [torch.empty((plan.dim,) + plan.shape, dtype=plan.dtype, device=dev) if with_E else None
-                  for _ in range(depth)]
-        self.s_in, self.s_run, self.s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
-        self.loaded = [torch.cuda.Event() for _ in range(depth)]
-        self.solved = [torch.cuda.Event() for _ in range(depth)]
-        self.freed = [torch.cuda.Event() for _ in range(depth)]
-        for e in self.freed:
-            e.record(self.s_out)
+        with torch.cuda.device(plan.device):
+            h = self.lib.fsp_host_pipe_create(plan.handle, int(depth), int(with_phi), int(with_E))
+        if not h:
+            raise _lib.FspError(self.lib.fsp_last_error(), "fsp_host_pipe_create")
+        self.handle = ctypes.c_void_p(h)
 
-    def run(self, rho_host, phi_host=None, E_host=None):
-        """rho_host: list of host tensors; phi_host / E_host: lists of host outputs (or None)."""
-        for i, r in enumerate(rho_host):
-            k = i % self.depth
-            self.s_in.wait_event(self.freed[k])
-            with torch.cuda.stream(self.s_in):
-                self.rho[k].copy_(r, non_blocking=True)
-                self.loaded[k].record(self.s_in)
-            self.s_run.wait_event(self.loaded[k])
-            self.plan.solve(self.rho[k], with_phi=self.with_phi, with_E=self.with_E, phi=self.phi[k], E=self.E[k],
-                            stream=self.s_run)
-            self.solved[k].record(self.s_run)
-            self.s_out.wait_event(self.solved[k])
-            with torch.cuda.stream(self.s_out):
-                if phi_host is not None and self.with_phi:
-                    phi_host[i].copy_(self.phi[k], non_blocking=True)
-                if E_host is not None and self.with_E:
-                    E_host[i].copy_(self.E[k], non_blocking=True)
-                self.freed[k].record(self.s_out)
-        return self.s_out
+    def _check_host(self, t, name, lead=()):
+        want = tuple(lead) + self.plan.shape
+        if t.is_cuda or t.dtype != self.plan.dtype or tuple(t.shape) != want or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host {self.plan.dtype} tensor of shape {want}")
+
+    def run(self, rho_host, phi_host=None, E_host=None, stream=None):
+        """rho_host: list of host tensors; phi_host / E_host: lists of host outputs.
+
+        Asynchronous: returns once queued; the given (default: current) stream
+        waits for the last copy-out.  Returns that stream."""
+        n = len(rho_host)
+        for r in rho_host:
+            self._check_host(r, "rho")
+        if self.with_phi:
+            if phi_host is None or len(phi_host) != n:
+                raise ValueError("phi_host: one output per input")
+            for t in phi_host:
+                self._check_host(t, "phi")
+        if self.with_E:
+            if E_host is None or len(E_host) != n:
+                raise ValueError("E_host: one output per input")
+            for t in E_host:
+                self._check_host(t, "E", (self.plan.dim,))
+        s = torch.cuda.current_stream(self.plan.device) if stream is None else stream
+        _lib.check(self.lib.fsp_host_pipe_solve(self.handle, n, _arr([_ptr(r) for r in rho_host]),
+                                                _arr([_ptr(t) for t in phi_host]) if self.with_phi else None,
+                                                _arr([_ptr(t) for t in E_host]) if self.with_E else None,
+                                                _stream(s)), "fsp_host_pipe_solve")
+        self._keep = (rho_host, phi_host, E_host)   # host buffers stay referenced while queued
+        return s
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fsp_host_pipe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FspSolve(torch.autograd.Function):

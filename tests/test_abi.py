@@ -73,8 +73,26 @@ def test_null_arguments(lib):
     assert lib.fsp_solve_batched(None, 0, None, None, None, None) == 1
     assert lib.fsp_batch_create(None, 0, None, None, None) is None
     assert lib.fsp_batch_solve(None, None) == 1
+    assert lib.fsp_host_pipe_create(None, 2, 1, 1) is None
+    assert lib.fsp_last_error() == 1
+    assert lib.fsp_host_pipe_solve(None, 0, None, None, None, None) == 1
+    assert lib.fsp_solve_noalloc(None, None, None, None, None) == 1
+    assert lib.fsp_gradient_fd(None, None, None, None) == 1
+    assert lib.fsp_autotune(None, None, 0) == 1
+    # every entry point leaves its status in fsp_last_error()
+    lib.fsp_plan_create_ex(32, 32, 32, 0.1, 0.1, 0.1, 1, 0, 1.0, float("nan"), 2)
+    assert lib.fsp_last_error() == 1
+    assert lib.fsp_error_string(0) == b"ok"
+    for call in (lambda: lib.fsp_solve_noalloc(None, None, None, None, None),
+                 lambda: lib.fsp_gradient_fd(None, None, None, None),
+                 lambda: lib.fsp_autotune(None, None, 0),
+                 lambda: lib.fsp_host_pipe_solve(None, 0, None, None, None, None)):
+        lib.fsp_plan_create(-1, 1, 1, 0.1, 0.1, 0.1, 0, 0)   # sets 1
+        assert lib.fsp_plan_create(513, 32, 32, 0.1, 0.1, 0.1, 1, 0) is None and lib.fsp_last_error() == 2
+        assert call() == 1 and lib.fsp_last_error() == 1
     lib.fsp_plan_destroy(None)
     lib.fsp_batch_destroy(None)
+    lib.fsp_host_pipe_destroy(None)
 
 
 def test_python_package_has_no_cpu_fallback():

@@ -60,11 +60,13 @@ def test_traffic_is_reported_only_for_the_measured_sources(tmp_path, monkeypatch
 
 def test_cpu_baseline_block_fields():
     pytest.importorskip("oracle")
-    b = bench.cpu_baseline_block(16, 16)
-    for key in ("value", "unit", "cores", "kind", "sample", "cpu", "single_thread"):
+    b = bench.cpu_baseline_block(16, 16, full_n=16)
+    for key in ("value", "unit", "cores", "kind", "sample", "cpu", "single_thread", "scaled_sample"):
         assert key in b
     assert b["kind"] == "oracle" and b["cores"] >= 1 and b["value"] > 0
     assert b["single_thread"]["cores"] == 1 and b["single_thread"]["value"] > 0
+    times, cores = bench.oracle_headline(5, budget_s=0.0, n=16)
+    assert len(times) == 1 and cores >= 1   # the budget stops after the first timed solve
 
 
 def test_padded_fft_context_solve_matches_oracle():
