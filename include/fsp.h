@@ -230,6 +230,16 @@ int fsp_host_pipe_solve(fsp_host_pipe *pipe, int count, const void *const *rho_h
 void fsp_host_pipe_destroy(fsp_host_pipe *pipe);
 
 /*
+ * Device-side status of the plan's solves: FSP_OK, or FSP_ERR_TIMEOUT if a
+ * kernel's bounded wait (the shared-memory tile barriers of the TMA-staged
+ * passes, which give up after about 2 s) failed in some solve since the last
+ * clear; that solve's outputs are then not valid.  Synchronises with the
+ * device (a blocking copy of one word); clear != 0 resets the word.  The
+ * solve calls never return this code themselves, since they do not wait.
+ */
+int fsp_plan_device_status(fsp_plan *plan, int clear);
+
+/*
  * Test hook: copy the plan's FP32 kernel spectrum to host memory, layout
  * [nx+1][ny+1][nz+1] (2D: [nx+1][ny+1]), entry (kx,ky,kz) = prod(h)/prod(2n)
  * times the DFT of the padded kernel at index k (indices k and 2n-k share it).

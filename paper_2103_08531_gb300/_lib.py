@@ -45,6 +45,7 @@ SIGNATURES = {
     "fsp_host_pipe_create": (_vp, [_vp, _i, _i, _i]),
     "fsp_host_pipe_solve": (_i, [_vp, _i, _vpp, _vpp, _vpp, _vp]),
     "fsp_host_pipe_destroy": (None, [_vp]),
+    "fsp_plan_device_status": (_i, [_vp, _i]),
 }
 
 

@@ -100,6 +100,7 @@ static void plan_free(Plan &p)
     if (p.tw2 != p.tw0 && p.tw2 != p.tw1) cudaFree(p.tw2);
     cudaFree(p.K);
     cudaFree(p.K64);
+    cudaFree(p.status);
     for (int a = 0; a < 3; ++a) cudaFree(p.dtw[a]);
 }
 
@@ -196,6 +197,8 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     if (rc == FSP_OK && cudaMalloc(&p.K, sizeof(float) * p.K_count) != cudaSuccess) rc = FSP_ERR_NOMEM;
     if (rc == FSP_OK && dtype == FSP_F64 && cudaMalloc(&p.K64, sizeof(double) * p.K_count) != cudaSuccess)
         rc = FSP_ERR_NOMEM;
+    if (rc == FSP_OK && cudaMalloc(&p.status, sizeof(int)) != cudaSuccess) rc = FSP_ERR_NOMEM;
+    if (rc == FSP_OK && cudaMemset(p.status, 0, sizeof(int)) != cudaSuccess) rc = FSP_ERR_CUDA;
     cudaStream_t st = nullptr;
     if (rc == FSP_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = FSP_ERR_CUDA;
     if (rc == FSP_OK && p.direct) {
@@ -293,6 +296,15 @@ extern "C" int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int
     return set_err(FSP_OK);
 }
 
+extern "C" int fsp_plan_device_status(fsp_plan *plan, int clear)
+{
+    if (!plan || !plan->p.status) return set_err(FSP_ERR_INVALID);
+    int v = 0;
+    if (cudaMemcpy(&v, plan->p.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(FSP_ERR_CUDA);
+    if (clear && v && cudaMemset(plan->p.status, 0, sizeof(int)) != cudaSuccess) return set_err(FSP_ERR_CUDA);
+    return set_err(v);
+}
+
 extern "C" int fsp_plan_kernel_spectrum(const fsp_plan *plan, void *host_out, size_t bytes)
 {
     if (!plan || !host_out) return set_err(FSP_ERR_INVALID);
@@ -322,6 +334,7 @@ static PassArgs base_args(const Plan &p, void *ws)
     a.tw1 = p.tw1;
     a.tw2 = p.tw2;
     a.K = p.K;
+    a.status = p.status;
     a.buf0 = reinterpret_cast<float2 *>(ws);
     a.buf1 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + align_up(p.buf_elems * sizeof(float2), 256));
     return a;

@@ -1,8 +1,10 @@
 // fsp_axis0.cu -- launchers of the axis-0 passes (P1 real -> half spectrum, P5 back).
 #include "fsp_internal.h"
 #include "fsp_launch.cuh"
+#include "fsp_tma.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 namespace fsp {
@@ -80,10 +82,65 @@ static int prep_one()
     return e;
 }
 
+// TMA-staged group tiles (single solves, 2n <= 512)
+template <int N>
+struct TmaOcc0 {
+    static inline int p1 = 1, p5 = 1;
+};
+template <int N>
+static constexpr size_t smem_p1_tma() { return GroupSmem<N>::bytes(1, N / 2); }
+template <int N>
+static constexpr size_t smem_p5_tma() { return GroupSmem<N>::bytes(3, N / 2); }
+
+template <int N>
+static int prep_tma()
+{
+    int e = 0, b1 = 0, b5 = 0;
+    using C = GroupCfg<N>;
+    e |= cudaFuncSetAttribute(p1_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1_tma<N>());
+    e |= cudaFuncSetAttribute(p5_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_tma<N>, C::THREADS, smem_p1_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_tma<N>, C::THREADS, smem_p5_tma<N>());
+    TmaOcc0<N>::p1 = std::max(1, b1);
+    TmaOcc0<N>::p5 = std::max(1, b5);
+    return e;
+}
+
 template <int N>
 static int prep()
 {
-    return prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
+    int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
+    if constexpr (N <= 512) e |= prep_tma<N>();
+    return e;
+}
+
+// The TMA-staged P1 / P5 of one solve (maps built here from the solve's buffers).
+template <int N>
+static int tma_launch0(int kind, const PassArgs &a, int var, cudaStream_t st)
+{
+    using C = GroupCfg<N>;
+    TmaMaps m;
+    std::memset(&m, 0, sizeof(m));
+    const int sms = sm_count();
+    if (kind == PASS_P1F) {
+        const unsigned long long dims[3] = {(unsigned long long)a.n2, (unsigned long long)a.n1,
+                                            (unsigned long long)a.n0};
+        const unsigned long long str[2] = {(unsigned long long)a.n2 * 4, (unsigned long long)a.n1 * a.n2 * 4};
+        const unsigned box[3] = {32, 1, N / 2};
+        if (encode_tensor_map(&m.m[0], a.in[0], 3, 4, dims, str, box)) return (int)cudaErrorInvalidValue;
+        const int units = a.n1 * (a.n2 / 32);
+        const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc0<N>::p1));
+        return launch_pdl(p1_tma<N>, grid, C::THREADS, smem_p1_tma<N>(), st, a, m);
+    }
+    const unsigned long long dims[3] = {(unsigned long long)a.n2, (unsigned long long)a.rows1,
+                                        (unsigned long long)a.n0 + 1};
+    const unsigned long long str[2] = {(unsigned long long)a.n2 * 8, (unsigned long long)a.rows1 * a.n2 * 8};
+    const unsigned box[3] = {16, 1, N / 2};
+    if (encode_tensor_map(&m.m[0], a.buf0, 3, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
+    if (encode_tensor_map(&m.m[1], a.buf1, 3, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
+    const int units = a.n1 * (a.n2 / 16);
+    const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc0<N>::p5));
+    return launch_pdl(p5_tma<N>, grid, C::THREADS, smem_p5_tma<N>(), st, a, m);
 }
 
 int prepare_axis0(int N)
@@ -146,6 +203,10 @@ static int tile_launch(int kind, const Wk &w, int var, cudaStream_t st)
 template <int N>
 static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
 {
+    if constexpr (N <= 512) {
+        if ((kind == PASS_P1F || kind == PASS_P5F) && n == 1 && !(var & 4) && items[0].n2 % 32 == 0)
+            return tma_launch0<N>(kind, items[0], var, st);
+    }
     if (kind == PASS_P1F || kind == PASS_P5F) {
         return chunked(items, n, kind == PASS_P1F ? units_p1f<N> : units_p5f<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;

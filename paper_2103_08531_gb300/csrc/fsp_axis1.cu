@@ -1,8 +1,10 @@
 // fsp_axis1.cu -- launchers of the axis-1 passes (P2 forward, P4 inverse; 3D only).
 #include "fsp_internal.h"
 #include "fsp_launch.cuh"
+#include "fsp_tma.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 namespace fsp {
@@ -68,10 +70,61 @@ static int prep_one()
     return e;
 }
 
+// TMA-staged group tiles (single solves, 2n <= 512)
+template <int N>
+struct TmaOcc1 {
+    static inline int p2 = 1, p4 = 1;
+};
+template <int N>
+static constexpr size_t smem_p2_tma() { return GroupSmem<N>::bytes(1, N / 2); }
+template <int N>
+static constexpr size_t smem_p4_tma() { return GroupSmem<N>::bytes(2, N); }
+
+template <int N>
+static int prep_tma()
+{
+    int e = 0, b2 = 0, b4 = 0;
+    using C = GroupCfg<N>;
+    e |= cudaFuncSetAttribute(p2_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2_tma<N>());
+    e |= cudaFuncSetAttribute(p4_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_tma<N>, C::THREADS, smem_p2_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_tma<N>, C::THREADS, smem_p4_tma<N>());
+    TmaOcc1<N>::p2 = std::max(1, b2);
+    TmaOcc1<N>::p4 = std::max(1, b4);
+    return e;
+}
+
 template <int N>
 static int prep()
 {
-    return prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
+    int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
+    if constexpr (N <= 512) e |= prep_tma<N>();
+    return e;
+}
+
+// The TMA-staged P2 / P4 of one solve: maps over buf1 (P2) or buf0 and buf1
+// (P4) as [(n0 + 1) rows1][n2] complex.
+template <int N>
+static int tma_launch1(int kind, const PassArgs &a, int flag, int var, cudaStream_t st)
+{
+    using C = GroupCfg<N>;
+    TmaMaps m;
+    std::memset(&m, 0, sizeof(m));
+    const unsigned long long dims[2] = {(unsigned long long)a.n2, (unsigned long long)(a.n0 + 1) * a.rows1};
+    const unsigned long long str[1] = {(unsigned long long)a.n2 * 8};
+    const int units = (a.n0 + 1) * (a.n2 / 16);
+    const int sms = sm_count();
+    if (kind == PASS_P2F) {
+        const unsigned box[2] = {16, N / 2};
+        if (encode_tensor_map(&m.m[0], a.buf1, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
+        const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc1<N>::p2));
+        return launch_pdl(p2_tma<N>, grid, C::THREADS, smem_p2_tma<N>(), st, a, m);
+    }
+    const unsigned box[2] = {16, N < 256 ? N : 256};
+    if (encode_tensor_map(&m.m[0], a.buf0, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
+    if (encode_tensor_map(&m.m[1], a.buf1, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
+    const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc1<N>::p4));
+    return launch_pdl(p4_tma<N>, grid, C::THREADS, smem_p4_tma<N>(), st, a, m, flag);
 }
 
 int prepare_axis1(int N)
@@ -116,6 +169,10 @@ static int tile_launch(int kind, const Wk &w, int flag, int var, cudaStream_t st
 template <int N>
 static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
+    if constexpr (N <= 512) {
+        if ((kind == PASS_P2F || kind == PASS_P4F) && n == 1 && !(var & 4) && items[0].n2 % 16 == 0)
+            return tma_launch1<N>(kind, items[0], flag, var, st);
+    }
     if (kind == PASS_P2F || kind == PASS_P4F) {
         return chunked(items, n, units_tile<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;

@@ -38,6 +38,7 @@ struct Plan {
     double *K64;              // FP64 kernel octant (FP64 plans)
     double2 *dtw[3];          // FP64 twiddles exp(2 pi i m / (2 n_a)) per pass axis (direct plans)
     double kd[3];             // 2 pi / (2 n_a h_a) per pass axis, FP64
+    int *status;              // device status word (FSP_OK, or FSP_ERR_TIMEOUT from a bounded wait)
 };
 
 // fsp_precompute.cu
@@ -66,7 +67,10 @@ int prepare_axis0(int N);
 int prepare_axis1(int N);
 int prepare_axis2(int N);
 // var: tuning variant bits (1 = 8 values per thread in column tiles, 2 = one
-// CTA per SM in persistent launches); chosen by the autotuner (fsp_autotune.cu).
+// CTA per SM in persistent launches, 4 = the cp.async block-synchronous column
+// tiles instead of the TMA-staged group tiles); chosen by the autotuner
+// (fsp_autotune.cu).  Single solves of 2n <= 512 run the TMA-staged column
+// passes unless bit 4 is set; batches and longer columns run the others.
 int launch_axis0(int kind, int N, const PassArgs *items, int n, int var, cudaStream_t st);
 int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
 int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
@@ -84,6 +88,12 @@ int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, f
 // Store status s as the calling thread's fsp_last_error() and return it; every
 // C entry point returns through this.
 int record_error(int s);
+
+// fsp_tma_host.cu: a tiled tensor map over a row-major array (dims[0] contiguous;
+// strides in bytes of dims 1 .. rank-1), 128-byte swizzle, box `box`; elem_bytes
+// 4 or 8.  Returns 0 or a CUresult.
+int encode_tensor_map(void *map, const void *base, int rank, int elem_bytes, const unsigned long long *dims,
+                      const unsigned long long *strides, const unsigned *box);
 
 // fsp_autotune.cu: the variant chosen for a pass kind at padded length N (0 if untuned)
 int tuned_variant(int kind, int N);

@@ -38,6 +38,7 @@ struct PassArgs {
     float2 *buf0, *buf1;
     const float *in[4];
     float *out[4];
+    int *status;      // device status word of the solve (0 = fine; set by bounded waits that gave up)
 };
 
 __device__ __forceinline__ size_t iidx(const PassArgs &a, int k0, int row, int z)
