@@ -1,8 +1,10 @@
 // fsp_autotune.cu -- picks a launch variant per (pass, padded length) by timing.
 //
-// Variants (bits): 1 = 8 values per thread in the column tiles of P1/P2/P4/P5
-// instead of 16 (lengths <= 512, not 192); 2 = one CTA per SM in the
-// persistent launches instead of as many as fit.  The table is process-wide,
+// Variants (bits): 4 = the cp.async block-synchronous column tiles of
+// P1/P2/P4/P5 instead of the TMA-staged group tiles (single solves, lengths
+// <= 512); 1 = with bit 4, 8 values per thread in those tiles instead of 16
+// (not 192); 2 = one CTA per SM in the persistent launches instead of as many
+// as fit.  The table is process-wide,
 // keyed by pass kind and padded length, and is read by every solve.  A small
 // JSON file caches it per GPU architecture, e.g.
 //   {"sm_103": {"p3_fwd/512": 0, "p4_fwd/512": 2}}
@@ -42,7 +44,7 @@ std::vector<int> candidates(int kind, int N)
 {
     const bool tile = kind == PASS_P1F || kind == PASS_P2F || kind == PASS_P4F || kind == PASS_P5F;
     if (N > 512) return {0};
-    if (tile) return N == 192 ? std::vector<int>{0, 2} : std::vector<int>{0, 1, 2, 3};
+    if (tile) return N == 192 ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0, 2, 4, 5, 6, 7};
     if (kind == PASS_P3F || kind == PASS_P3A) return {0, 2};
     return {0};
 }
@@ -85,7 +87,7 @@ void load_cache(const char *path, const std::string &arch)
             int N = std::atoi(key.c_str() + slash + 1);
             int li = length_index(N);
             for (int k = 0; k < PASS_KINDS && li >= 0; ++k)
-                if (name == kKindName[k] && val >= 0 && val < 4) g_var[k][li] = val;
+                if (name == kKindName[k] && val >= 0 && val < 8) g_var[k][li] = val;
         }
         pos = colon + 1;
     }

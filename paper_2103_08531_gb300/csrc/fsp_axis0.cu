@@ -88,15 +88,15 @@ struct TmaOcc0 {
     static inline int p1 = 1, p5 = 1;
 };
 template <int N>
-static constexpr size_t smem_p1_tma() { return GroupSmem<N>::bytes(1, N / 2); }
+static constexpr size_t smem_p1_tma() { return TmaTile<N>::smem(1, N / 2); }
 template <int N>
-static constexpr size_t smem_p5_tma() { return GroupSmem<N>::bytes(3, N / 2); }
+static constexpr size_t smem_p5_tma() { return TmaTile<N>::smem(3, N / 2); }
 
 template <int N>
 static int prep_tma()
 {
     int e = 0, b1 = 0, b5 = 0;
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     e |= cudaFuncSetAttribute(p1_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1_tma<N>());
     e |= cudaFuncSetAttribute(p5_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_tma<N>());
     e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_tma<N>, C::THREADS, smem_p1_tma<N>());
@@ -118,7 +118,7 @@ static int prep()
 template <int N>
 static int tma_launch0(int kind, const PassArgs &a, int var, cudaStream_t st)
 {
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     TmaMaps m;
     std::memset(&m, 0, sizeof(m));
     const int sms = sm_count();

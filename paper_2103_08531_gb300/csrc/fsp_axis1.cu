@@ -76,15 +76,15 @@ struct TmaOcc1 {
     static inline int p2 = 1, p4 = 1;
 };
 template <int N>
-static constexpr size_t smem_p2_tma() { return GroupSmem<N>::bytes(1, N / 2); }
+static constexpr size_t smem_p2_tma() { return TmaTile<N>::smem(1, N / 2); }
 template <int N>
-static constexpr size_t smem_p4_tma() { return GroupSmem<N>::bytes(2, N); }
+static constexpr size_t smem_p4_tma() { return TmaTile<N>::smem(2, N); }
 
 template <int N>
 static int prep_tma()
 {
     int e = 0, b2 = 0, b4 = 0;
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     e |= cudaFuncSetAttribute(p2_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2_tma<N>());
     e |= cudaFuncSetAttribute(p4_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4_tma<N>());
     e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_tma<N>, C::THREADS, smem_p2_tma<N>());
@@ -107,7 +107,7 @@ static int prep()
 template <int N>
 static int tma_launch1(int kind, const PassArgs &a, int flag, int var, cudaStream_t st)
 {
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     TmaMaps m;
     std::memset(&m, 0, sizeof(m));
     const unsigned long long dims[2] = {(unsigned long long)a.n2, (unsigned long long)(a.n0 + 1) * a.rows1};

@@ -245,9 +245,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // ------------------------------------------------------------------- passes
 
-// Sync groups of a transform: the whole block, one warp, or (SYNC_GROUP0 + w)
-// a group of w warps with named barrier 1 + threadIdx.x / (32 w).
-enum { SYNC_BLOCK = 0, SYNC_WARP = 1, SYNC_GROUP0 = 64 };
+enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // Twiddle sources: TW_TABLE loads each W^(r m) from the table (cheap when the
 // lanes of a warp share m, as in column tiles); TW_POW loads W^m, W^2m, W^4m,
 // W^8m and forms the other powers by products (lanes with distinct m).
@@ -287,14 +285,8 @@ __device__ __forceinline__ float2 ldtw(const float2 *p)
 template <int SYNC>
 __device__ __forceinline__ void lsync()
 {
-    if constexpr (SYNC == SYNC_WARP) {
-        __syncwarp();
-    } else if constexpr (SYNC > SYNC_GROUP0) {
-        constexpr int GT = 32 * (SYNC - SYNC_GROUP0);
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / GT), "n"(GT) : "memory");
-    } else {
-        __syncthreads();
-    }
+    if constexpr (SYNC == SYNC_WARP) __syncwarp();
+    else __syncthreads();
 }
 
 // u[r] *= W^(r m) (conjugated for the inverse), r = 1 .. R-1.
@@ -434,8 +426,8 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
         // Block-synchronous form of the same lane-pair swap: only the half of
         // the outputs that changes thread goes through shared memory.  The
         // branches are warp-uniform in column tiles (j = tid / columns).
-        constexpr bool HALF = FSP_HALF_XCH && (SYNC == SYNC_BLOCK || SYNC > SYNC_GROUP0) && T == 32 && Q == 1 &&
-                              2 * NS * R == N && IsClosingRadix2<RS...>::value;
+        constexpr bool HALF = FSP_HALF_XCH && SYNC == SYNC_BLOCK && T == 32 && Q == 1 && 2 * NS * R == N &&
+                              IsClosingRadix2<RS...>::value;
         static_assert(E % R == 0, "E must be a multiple of every radix");
         if constexpr (HALF) {
             const int k = j % NS;

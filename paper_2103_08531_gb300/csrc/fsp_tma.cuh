@@ -2,28 +2,22 @@
 //
 // The column passes (P1, P2, P4, P5) move tiles of 16 consecutive axis-2
 // columns (one 128-byte row segment per line position) between HBM and the
-// SM.  Here one thread per CTA issues the tile loads as bulk tensor copies
+// SM.  Here one thread per CTA issues each tile's loads as bulk tensor copies
 // (cp.async.bulk.tensor) that land in shared memory in the 128-byte swizzled
-// layout and signal an mbarrier with their byte count; the other threads only
-// wait on that barrier.  The tile's columns are then transformed by four
-// independent groups of threads, four columns each, which synchronise among
-// themselves only (a named barrier per group, or the warp when a group is one
-// warp), so the groups of a CTA and the loads of the next tile overlap
-// instead of running in lock step.
+// layout and signal an mbarrier with their byte count, instead of every
+// thread copying 16-byte pieces; the next tile is in flight while the current
+// one is transformed.
 //
-// Shared-memory layouts (float2 = one complex value, or two reals in P1):
-//   stage: the TMA box as delivered, row r (line position) at r * 128 bytes,
-//          the 16-byte chunk of columns (2c, 2c+1) at chunk c ^ (r & 7);
-//          every box starts on a 1024-byte boundary.
-//   group exchange buffer: position p of the group's column cl at
-//          4 * sw(p) + cl, sw(p) = (p & ~3) | ((p ^ (p >> 2) ^ (p >> 4)) & 3):
-//          the four positions a half-warp touches in every Stockham exchange
-//          of the radix plans used here fall in four different 32-byte bank
-//          groups (checked exhaustively for 2n = 64 ... 512 on the host).
+// Shared-memory layout of a stage (float2 = one complex value, or two reals
+// in P1): the TMA box as delivered, row r (line position) at r * 128 bytes,
+// the 16-byte chunk of columns (2c, 2c+1) at chunk c ^ (r & 7); every box
+// starts on a 1024-byte boundary.  A half-warp reads one row (its 16 lanes
+// are the 16 columns), so the swizzle only permutes the chunks of that row:
+// no bank conflicts.
 //
 // Every wait is bounded: a wait that has not seen its barrier phase complete
 // after kWaitNs nanoseconds records FSP_ERR_TIMEOUT in the solve's status
-// word and the CTA leaves its loop.
+// word, and the CTA (agreeing through its block barrier) leaves its loop.
 #pragma once
 
 #include "../../include/fsp.h"
@@ -104,50 +98,9 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// OR of `pred` over the `count` threads of named barrier `id` (a multiple of 32 threads).
-__device__ __forceinline__ bool bar_or(int id, int count, bool pred)
-{
-    unsigned r;
-    asm volatile("{\n\t.reg .pred p, q;\n\t"
-                 "setp.ne.u32 p, %1, 0;\n\t"
-                 "bar.red.or.pred q, %2, %3, p;\n\t"
-                 "selp.u32 %0, 1, 0, q;\n\t}"
-                 : "=r"(r)
-                 : "r"((unsigned)pred), "r"(id), "r"(count)
-                 : "memory");
-    return r != 0;
-}
-
 // Element (row, col) of a 16-column stage in the 128-byte swizzled layout.
 __device__ __forceinline__ int sw128(int row, int col) { return row * 16 + ((((col >> 1) ^ row) & 7) << 1) + (col & 1); }
 
-// Exchange buffer of one group of four columns (see the file comment).
-struct GroupView {
-    float2 *base;   // group buffer + column
-    __device__ __forceinline__ float2 &at(int p) const
-    {
-        return base[((p & ~3) | ((p ^ (p >> 2) ^ (p >> 4)) & 3)) << 2];
-    }
-};
-
-// Geometry of the group-tiled passes at padded length N.
-template <int N>
-struct GroupCfg {
-    static constexpr int E = Plan16<N>::E;
-    static constexpr int T = N / E;                    // threads per column
-    static constexpr int C = 16;                       // columns per tile
-    static constexpr int GC = 4;                       // columns per group
-    static constexpr int GT = GC * T;                  // threads per group
-    static constexpr int GROUPS = C / GC;
-    static constexpr int THREADS = GT * GROUPS;
-    static constexpr int WARPS = THREADS / 32;
-    static_assert(GT % 32 == 0, "a group is a whole number of warps");
-    static constexpr int SYNC = GT == 32 ? SYNC_WARP : SYNC_GROUP0 + GT / 32;
-    using RAD = typename Plan16<N>::R;
-    static constexpr int TWS = AuxEnd<1, N, RAD>::value;   // main table + gathered blocks
-    static constexpr int EXG = N * GC;                       // float2 per group exchange buffer
-    static constexpr int BOX = N / 2 < 256 ? N / 2 : 256;     // rows per TMA box for a half line
-};
 
 // Record a device-side failure in the solve's status word (first one wins).
 __device__ __forceinline__ void record_status(int *status, int code)
@@ -155,168 +108,116 @@ __device__ __forceinline__ void record_status(int *status, int code)
     if (status) atomicCAS(status, 0, code);
 }
 
-// The shared-memory plan of a group-tiled kernel: `stages` stage buffers of
-// `rows` rows each (1024-byte aligned), the group exchange buffers, the
-// twiddle copy, the barrier and the reader count.
+// Shared memory of a TMA-staged tile kernel: alignment slack, `stages` stage
+// buffers of `rows` 128-byte rows (each rounded up to 1024 bytes), the tile
+// exchange buffer with the twiddle copy after it (TileCfg::EX), the barrier.
 template <int N>
-struct GroupSmem {
-    using C = GroupCfg<N>;
+struct TmaTile {
+    using C = TileCfg<N, 16>;
     static constexpr size_t stage_bytes(int rows) { return ((size_t)rows * 128 + 1023) / 1024 * 1024; }
-    static constexpr size_t bytes(int stages, int rows)
+    static constexpr size_t smem(int stages, int rows)
     {
-        return 1024 /* alignment slack */ + stages * stage_bytes(rows) + (size_t)C::GROUPS * C::EXG * sizeof(float2) +
-               (size_t)C::TWS * sizeof(float2) + 16;
+        return 1024 + stages * stage_bytes(rows) + (size_t)C::EX * sizeof(float2) + 16;
     }
 };
 
-struct GroupPtrs {
+struct TmaSmem {
     float2 *stage[3];
-    float2 *ex, *tw;
+    float2 *ex;
     uint64_t *bar;
-    int *taken;
 };
 
 template <int N>
-__device__ __forceinline__ GroupPtrs group_smem(unsigned char *raw, int stages, int rows)
+__device__ __forceinline__ TmaSmem tma_smem(unsigned char *raw, int stages, int rows)
 {
-    using C = GroupCfg<N>;
-    GroupPtrs p;
-    // align the shared-space offset (the address the TMA unit and the swizzle see)
+    // align the shared-space offset (what the TMA unit and the swizzle see)
     const unsigned off = smem_u32(raw);
-    const uintptr_t a = reinterpret_cast<uintptr_t>(raw) + (((off + 1023u) & ~1023u) - off);
-    unsigned char *b = reinterpret_cast<unsigned char *>(a);
-    for (int s = 0; s < 3; ++s) {
-        p.stage[s] = reinterpret_cast<float2 *>(b);
-        if (s < stages) b += GroupSmem<N>::stage_bytes(rows);
+    unsigned char *b = raw + (((off + 1023u) & ~1023u) - off);
+    TmaSmem s;
+    for (int i = 0; i < 3; ++i) {
+        s.stage[i] = reinterpret_cast<float2 *>(b);
+        if (i < stages) b += TmaTile<N>::stage_bytes(rows);
     }
-    p.ex = reinterpret_cast<float2 *>(b);
-    b += (size_t)C::GROUPS * C::EXG * sizeof(float2);
-    p.tw = reinterpret_cast<float2 *>(b);
-    b += (size_t)C::TWS * sizeof(float2);
-    p.bar = reinterpret_cast<uint64_t *>(b);
-    p.taken = reinterpret_cast<int *>(b + 8);
-    return p;
+    s.ex = reinterpret_cast<float2 *>(b);
+    s.bar = reinterpret_cast<uint64_t *>(b + (size_t)TileCfg<N, 16>::EX * sizeof(float2));
+    return s;
 }
 
-// Common prologue: twiddle copy, barrier init (thread 0), block barrier.
-template <int N>
-__device__ __forceinline__ void group_prologue(const GroupPtrs &s, const float2 *gtw)
+// Barrier set-up by thread 0; the caller's next block barrier publishes it.
+__device__ __forceinline__ void tma_bar_setup(uint64_t *bar)
 {
-    using C = GroupCfg<N>;
-    for (int i = threadIdx.x; i < C::TWS; i += C::THREADS) s.tw[i] = gtw[i];
     if (threadIdx.x == 0) {
-        mbar_init(s.bar, 1);
-        *s.taken = 0;
+        mbar_init(bar, 1);
         mbar_init_fence();
     }
-    __syncthreads();
 }
 
-// Called by every warp once it has read the current stage into registers: the
-// last warp to do so releases the stage and calls issue() for the next tile.
-template <int N, class Issue>
-__device__ __forceinline__ void group_release(const GroupPtrs &s, Issue &&issue)
+// After the stage has been read into registers: true (for every thread) if
+// any thread's wait timed out; then thread 0 records it and waits once more,
+// bounded, for the copies that may still be in flight.
+__device__ __forceinline__ bool tma_tile_failed(bool ok, uint64_t *bar, unsigned parity, int *status)
 {
-    using C = GroupCfg<N>;
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
-        __threadfence_block();
-        if (atomicAdd(s.taken, 1) == C::WARPS - 1) {
-            atomicExch(s.taken, 0);
-            __threadfence_block();
-            fence_proxy_async();
-            issue();
-        }
+    if (!__syncthreads_or(!ok)) return false;
+    if (threadIdx.x == 0) {
+        record_status(status, FSP_ERR_TIMEOUT);
+        mbar_wait(bar, parity);
     }
-}
-
-// Bounded wait on the stage barrier, agreed on by the whole group: returns
-// false (for every thread of the group) if any of its threads timed out.
-template <int N>
-__device__ __forceinline__ bool group_wait(const GroupPtrs &s, unsigned parity, int *status)
-{
-    using C = GroupCfg<N>;
-    const bool ok = mbar_wait(s.bar, parity);
-    bool fail;
-    if constexpr (C::GT == 32) fail = __any_sync(0xffffffffu, !ok);
-    else fail = bar_or(1 + (int)threadIdx.x / C::GT, C::GT, !ok);
-    if (fail && (threadIdx.x % C::GT) == 0) record_status(status, FSP_ERR_TIMEOUT);
-    return !fail;
+    return true;
 }
 
 // ------------------------------------------------------------------ kernels
 //
-// Each kernel is persistent over tiles (grid <= tiles) and mirrors the
-// arithmetic of its cp.async counterpart in fsp_passes.cuh (p1_fwd, p2_fwd,
-// p4_fwd, p5_fwd): only the staging, the thread-to-column mapping and the
-// synchronisation differ.  Thread mapping: group g = tid / GT owns columns
-// 4 g .. 4 g + 3 of the tile; inside it, column cl = t % 4 and line thread
-// j = t / 4 (t = tid % GT), so a half-warp covers four line positions of
-// four adjacent columns (32 bytes of each of four stage rows).
+// Persistent over tiles (grid <= tiles).  Each mirrors the arithmetic and the
+// thread mapping of its cp.async counterpart in fsp_passes.cuh (p1_fwd,
+// p2_fwd, p4_fwd, p5_fwd: column = tid % 16, line thread j = tid / 16,
+// block-synchronous transforms through the [position][16] exchange buffer);
+// only the staging differs.  After the block barrier that ends the reads of a
+// stage, thread 0 issues the next tile's copies into it.
 
+// P1: rho column pairs (z, z + 1) of a tile of 32 reals -> half spectrum in
+// k0, rows 0 .. n1 - 1 of buf1 (3D) or buf0 (2D).  Unit: (y, tile).  Map 0:
+// rho as [n0][n1][n2] floats, box 32 x 1 x N/2.
 template <int N>
-struct GroupThread {
-    using C = GroupCfg<N>;
-    int g, cl, j, col;
-    __device__ __forceinline__ GroupThread()
-    {
-        const int tid = threadIdx.x;
-        g = tid / C::GT;
-        const int t = tid % C::GT;
-        cl = t % C::GC;
-        j = t / C::GC;
-        col = C::GC * g + cl;
-    }
-};
-
-template <int N, int E, bool INV, bool PRUNE_IN>
-__device__ __forceinline__ void group_fft(float2 (&v)[E], int j, const float2 *tw, const GroupView &sm)
-{
-    using C = GroupCfg<N>;
-    line_fft<N, E, INV, PRUNE_IN, typename C::RAD, GroupView, C::SYNC, TW_SMEM>(v, j, tw, sm);
-}
-
-// P1: rho column pairs (z, z + 1) of a tile of 32 reals -> half spectrum in k0,
-// rows 0 .. n1 - 1 of buf1 (3D) or buf0 (2D).  Unit: (y, tile).  Map 0: rho as
-// [n0][n1][n2] floats, box 32 x 1 x N/2.
-template <int N>
-__global__ void __launch_bounds__(GroupCfg<N>::THREADS, 2) p1_tma(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_constant__ PassArgs a,
                                                                   const __grid_constant__ TmaMaps maps)
 {
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];
     pdl_trigger();
-    const GroupPtrs s = group_smem<N>(smem_raw, 1, NH);
-    group_prologue<N>(s, a.tw0);
-    const GroupThread<N> th;
+    const TmaSmem s = tma_smem<N>(smem_raw, 1, NH);
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
     const int zt = a.n2 / 32, units = a.n1 * zt;
+    tma_bar_setup(s.bar);
+    const float2 *tw = C::twiddles(s.ex, a.tw0);   // (its block barrier also publishes the mbarrier)
     auto issue = [&](int w) {
         mbar_expect_tx(s.bar, NH * 128);
         tma_load_3d(s.stage[0], &maps.m[0], (w % zt) * 32, w / zt, 0, s.bar);
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (threadIdx.x == 0 && w < units) issue(w);
-    const GroupView sm{s.ex + th.g * C::EXG + th.cl};
+    if (tid == 0 && w < units) issue(w);
+    const ColView sm{s.ex + col, 16};
     float2 *__restrict__ dst = a.three_d ? a.buf1 : a.buf0;
     for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
-        if (!group_wait<N>(s, ph, a.status)) break;
-        const int y = w / zt, z0 = (w % zt) * 32 + 2 * th.col;
+        const bool ok = mbar_wait(s.bar, ph);
+        const int y = w / zt, z0 = (w % zt) * 32 + 2 * col;
         float2 v[E];
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(th.j + r * T, th.col)] : make_float2(0.f, 0.f);
-        const int wn = w + gridDim.x;
-        group_release<N>(s, [&] {
-            if (wn < units) issue(wn);
-        });
-        group_fft<N, E, false, true>(v, th.j, s.tw, sm);
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
+        if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
+        if (tid == 0 && w + (int)gridDim.x < units) {
+            fence_proxy_async();
+            issue(w + gridDim.x);
+        }
+        tile_fft<N, E, false, true, RAD>(v, j, tw, sm);
 #pragma unroll
-        for (int r = 0; r < E; ++r) sm.at(th.j + r * T) = v[r];
-        lsync<C::SYNC>();
+        for (int r = 0; r < E; ++r) sm.at(j + r * T) = v[r];
+        __syncthreads();
 #pragma unroll
         for (int r = 0; r <= E / 2; ++r) {
-            const int k = th.j + r * T;
+            const int k = j + r * T;
             if (k <= NH) {
                 const float2 q = v[r];
                 const float2 m = sm.at(k == 0 ? 0 : N - k);
@@ -328,44 +229,48 @@ __global__ void __launch_bounds__(GroupCfg<N>::THREADS, 2) p1_tma(const __grid_c
                 *reinterpret_cast<float4 *>(dst + iidx(a, k, y, z0)) = o;
             }
         }
+        __syncthreads();   // the exchange buffer is reused by the next tile
     }
 }
 
 // P2: buf1 rows 0 .. n1 - 1 -> forward axis 1 -> buf0 rows 0 .. 2 n1 - 1.
 // Unit: (k0, tile).  Map 0: buf1 as [(n0 + 1) rows1][n2] complex, box 16 x N/2.
 template <int N>
-__global__ void __launch_bounds__(GroupCfg<N>::THREADS, 2) p2_tma(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_constant__ PassArgs a,
                                                                   const __grid_constant__ TmaMaps maps)
 {
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];
     pdl_trigger();
-    const GroupPtrs s = group_smem<N>(smem_raw, 1, NH);
-    group_prologue<N>(s, a.tw1);
-    const GroupThread<N> th;
+    const TmaSmem s = tma_smem<N>(smem_raw, 1, NH);
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
     const int zt = a.n2 / 16, units = (a.n0 + 1) * zt;
+    tma_bar_setup(s.bar);
+    const float2 *tw = C::twiddles(s.ex, a.tw1);
     auto issue = [&](int w) {
         mbar_expect_tx(s.bar, NH * 128);
         tma_load_2d(s.stage[0], &maps.m[0], (w % zt) * 16, (w / zt) * a.rows1, s.bar);
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (threadIdx.x == 0 && w < units) issue(w);
-    const GroupView sm{s.ex + th.g * C::EXG + th.cl};
+    if (tid == 0 && w < units) issue(w);
+    const ColView sm{s.ex + col, 16};
     for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
-        if (!group_wait<N>(s, ph, a.status)) break;
-        const int kx = w / zt, z = (w % zt) * 16 + th.col;
+        const bool ok = mbar_wait(s.bar, ph);
+        const int kx = w / zt, z = (w % zt) * 16 + col;
         float2 v[E];
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(th.j + r * T, th.col)] : make_float2(0.f, 0.f);
-        const int wn = w + gridDim.x;
-        group_release<N>(s, [&] {
-            if (wn < units) issue(wn);
-        });
-        group_fft<N, E, false, true>(v, th.j, s.tw, sm);
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
+        if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
+        if (tid == 0 && w + (int)gridDim.x < units) {
+            fence_proxy_async();
+            issue(w + gridDim.x);
+        }
+        tile_fft<N, E, false, true, RAD>(v, j, tw, sm);
 #pragma unroll
-        for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, th.j + r * T, z)] = v[r];
+        for (int r = 0; r < E; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
     }
 }
 
@@ -373,18 +278,20 @@ __global__ void __launch_bounds__(GroupCfg<N>::THREADS, 2) p2_tma(const __grid_c
 // buf1 (E2 stream) -> rows [0, n1).  Unit: (k0, tile).  Maps 0 and 1: buf0 and
 // buf1 as [(n0 + 1) rows1][n2] complex, box 16 x min(N, 256).
 template <int N>
-__global__ void __launch_bounds__(GroupCfg<N>::THREADS, 1) p4_tma(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_constant__ PassArgs a,
                                                                   const __grid_constant__ TmaMaps maps, int withE)
 {
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T;
     constexpr int BOXR = N < 256 ? N : 256, NB = N / BOXR;
+    using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];
     pdl_trigger();
-    const GroupPtrs s = group_smem<N>(smem_raw, 2, N);
-    group_prologue<N>(s, a.tw1);
-    const GroupThread<N> th;
+    const TmaSmem s = tma_smem<N>(smem_raw, 2, N);
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
     const int zt = a.n2 / 16, units = (a.n0 + 1) * zt;
+    tma_bar_setup(s.bar);
+    const float2 *tw = C::twiddles(s.ex, a.tw1);
     auto issue = [&](int w) {
         mbar_expect_tx(s.bar, (withE ? 2 : 1) * N * 128);
         const int x = (w % zt) * 16, y = (w / zt) * a.rows1;
@@ -396,60 +303,63 @@ __global__ void __launch_bounds__(GroupCfg<N>::THREADS, 1) p4_tma(const __grid_c
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (threadIdx.x == 0 && w < units) issue(w);
-    const GroupView sm{s.ex + th.g * C::EXG + th.cl};
+    if (tid == 0 && w < units) issue(w);
+    const ColView sm{s.ex + col, 16};
     const int n1 = a.n1;
     for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
-        if (!group_wait<N>(s, ph, a.status)) break;
-        const int kx = w / zt, z = (w % zt) * 16 + th.col;
+        const bool ok = mbar_wait(s.bar, ph);
+        const int kx = w / zt, z = (w % zt) * 16 + col;
         float2 v[E], q[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            v[r] = s.stage[0][sw128(th.j + r * T, th.col)];
-            q[r] = withE ? s.stage[1][sw128(th.j + r * T, th.col)] : make_float2(0.f, 0.f);
+            v[r] = s.stage[0][sw128(j + r * T, col)];
+            q[r] = withE ? s.stage[1][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
         }
-        const int wn = w + gridDim.x;
-        group_release<N>(s, [&] {
-            if (wn < units) issue(wn);
-        });
+        if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
+        if (tid == 0 && w + (int)gridDim.x < units) {
+            fence_proxy_async();
+            issue(w + gridDim.x);
+        }
         if (withE) {
-            group_fft<N, E, true, false>(q, th.j, s.tw, sm);
+            tile_fft<N, E, true, false, RAD>(q, j, tw, sm);
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, th.j + r * T, z)] = q[r];
+            for (int r = 0; r < E / 2; ++r) a.buf1[iidx(a, kx, j + r * T, z)] = q[r];
 #pragma unroll
             for (int r = 0; r < E; ++r) {
-                const float kk = wave(th.j + r * T, n1, a.k1s);
+                const float kk = wave(j + r * T, n1, a.k1s);
                 q[r] = make_float2(kk * v[r].y, -kk * v[r].x);
             }
-            group_fft<N, E, true, false>(q, th.j, s.tw, sm);
+            tile_fft<N, E, true, false, RAD>(q, j, tw, sm);
 #pragma unroll
-            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + th.j + r * T, z)] = q[r];
+            for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, n1 + j + r * T, z)] = q[r];
         }
-        group_fft<N, E, true, false>(v, th.j, s.tw, sm);
+        tile_fft<N, E, true, false, RAD>(v, j, tw, sm);
 #pragma unroll
-        for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, th.j + r * T, z)] = v[r];
+        for (int r = 0; r < E / 2; ++r) a.buf0[iidx(a, kx, j + r * T, z)] = v[r];
     }
 }
 
 // P5: half spectra in k0 -> real outputs.  Unit: (y, tile).  Maps 0 and 1:
 // buf0 and buf1 as [n0 + 1][rows1][n2] complex, box 16 x 1 x N/2 (rows
-// k0 < n0); the Nyquist row k0 = n0 comes from global memory directly.
+// k0 < n0); the Nyquist row k0 = n0 is read from global memory directly.
 // Stages: 0 the phi stream (buf0 row y), 1 the E1 stream (buf0 row n1 + y in
 // 3D, buf1 row y in 2D), 2 the E2 stream (buf1 row y, 3D).
 template <int N>
-__global__ void __launch_bounds__(GroupCfg<N>::THREADS, 1) p5_tma(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p5_tma(const __grid_constant__ PassArgs a,
                                                                   const __grid_constant__ TmaMaps maps)
 {
-    using C = GroupCfg<N>;
+    using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
+    using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];
     pdl_trigger();
-    const GroupPtrs s = group_smem<N>(smem_raw, 3, NH);
-    group_prologue<N>(s, a.tw0);
-    const GroupThread<N> th;
+    const TmaSmem s = tma_smem<N>(smem_raw, 3, NH);
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
     float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
     const bool first = phi || e0, second = e1 != nullptr, three = second && a.three_d;
     const int zt = a.n2 / 16, units = a.n1 * zt;
+    tma_bar_setup(s.bar);
+    const float2 *tw = C::twiddles(s.ex, a.tw0);
     auto issue = [&](int w) {
         mbar_expect_tx(s.bar, ((first ? 1 : 0) + (second ? 1 : 0) + (three ? 1 : 0)) * NH * 128);
         const int x = (w % zt) * 16, y = w / zt;
@@ -462,29 +372,30 @@ __global__ void __launch_bounds__(GroupCfg<N>::THREADS, 1) p5_tma(const __grid_c
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (threadIdx.x == 0 && w < units) issue(w);
-    const GroupView sm{s.ex + th.g * C::EXG + th.cl};
+    if (tid == 0 && w < units) issue(w);
+    const ColView sm{s.ex + col, 16};
+    constexpr int jN = NH % T, rN = NH / T;   // the thread and register holding k = NH
     for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
-        const int y = w / zt, z = (w % zt) * 16 + th.col;
+        const int y = w / zt, z = (w % zt) * 16 + col;
         // the Nyquist row (k0 = n0) of each stream, read directly
         float2 pN = make_float2(0.f, 0.f), YN = pN, ZN = pN;
-        constexpr int jN = NH % T;
-        if (th.j == jN) {
+        if (j == jN) {
             if (first) pN = a.buf0[iidx(a, NH, y, z)];
             if (second) YN = a.three_d ? a.buf0[iidx(a, NH, a.n1 + y, z)] : a.buf1[iidx(a, NH, y, z)];
             if (three) ZN = a.buf1[iidx(a, NH, y, z)];
         }
-        if (!group_wait<N>(s, ph, a.status)) break;
+        const bool ok = mbar_wait(s.bar, ph);
         float2 v[E], q[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            const int k = th.j + r * T;
+            const int k = j + r * T;
             const int src = k <= NH ? k : N - k;
-            const bool nyq = (r == NH / T) && th.j == jN;   // src == NH only there
+            const bool nyq = r == rN && j == jN;   // src == NH only there
+            const int row = src < NH ? src : 0;
             float2 p = make_float2(0.f, 0.f), Y = p, Z = p;
-            if (first) p = nyq ? pN : s.stage[0][sw128(src < NH ? src : 0, th.col)];
-            if (second) Y = nyq ? YN : s.stage[1][sw128(src < NH ? src : 0, th.col)];
-            if (three) Z = nyq ? ZN : s.stage[2][sw128(src < NH ? src : 0, th.col)];
+            if (first) p = nyq ? pN : s.stage[0][sw128(row, col)];
+            if (second) Y = nyq ? YN : s.stage[1][sw128(row, col)];
+            if (three) Z = nyq ? ZN : s.stage[2][sw128(row, col)];
             if (k > NH) {
                 p.y = -p.y;
                 Y.y = -Y.y;
@@ -494,24 +405,25 @@ __global__ void __launch_bounds__(GroupCfg<N>::THREADS, 1) p5_tma(const __grid_c
             v[r] = p;
             q[r] = make_float2(Y.x - Z.y, Y.y + Z.x);        // Y + i Z
         }
-        const int wn = w + gridDim.x;
-        group_release<N>(s, [&] {
-            if (wn < units) issue(wn);
-        });
+        if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
+        if (tid == 0 && w + (int)gridDim.x < units) {
+            fence_proxy_async();
+            issue(w + gridDim.x);
+        }
         if (first) {
-            group_fft<N, E, true, false>(v, th.j, s.tw, sm);
+            tile_fft<N, E, true, false, RAD>(v, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) {
-                const size_t g = gidx(a, th.j + r * T, y, z);
+                const size_t g = gidx(a, j + r * T, y, z);
                 if (phi) phi[g] = v[r].x;
                 if (e0) e0[g] = v[r].y;
             }
         }
         if (second) {
-            group_fft<N, E, true, false>(q, th.j, s.tw, sm);
+            tile_fft<N, E, true, false, RAD>(q, j, tw, sm);
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) {
-                const size_t g = gidx(a, th.j + r * T, y, z);
+                const size_t g = gidx(a, j + r * T, y, z);
                 e1[g] = q[r].x;
                 if (a.three_d) e2[g] = q[r].y;
             }

@@ -351,7 +351,9 @@ def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     p_ref, E_ref = oracle_mod.solve_with_kernel(g, rho32.astype(np.float64), h)
     path = str(tmp_path / "tune.json")
     try:
-        for vt, vp in [(0, 0), (1, 0), (2, 2), (3, 2)]:
+        # column tiles: 0 TMA-staged group tiles, 2 the same one CTA per SM, 4 / 5 the cp.async
+        # block tiles with 16 / 8 values per thread, 6 / 7 those one CTA per SM
+        for vt, vp in [(0, 0), (2, 2), (4, 0), (5, 0), (6, 2), (7, 2)]:
             _write_cache(path, arch, shape, vt, vp)
             plan.autotune(path, 0)
             assert fsp.tuned_variant("p1_fwd", 2 * shape[0]) == vt
