@@ -157,7 +157,13 @@ int fsp_solve_batched(fsp_plan *const *plans, int count, const void *const *rho,
  * Prebuilt batch: the device work lists of fsp_solve_batched built once, so
  * that repeated launches (or a captured CUDA graph) do no host work.
  * fsp_batch_create copies the pointer arrays; they must stay valid device
- * buffers for the life of the batch.
+ * buffers for the life of the batch.  It also creates a few CUDA streams and
+ * events of its own: the launches of one pass that serve different padded
+ * lengths are independent, so fsp_batch_solve forks them onto those streams
+ * from the caller's stream and joins them back before the next pass (in a
+ * captured graph: parallel branches).  The caller's stream sees the usual
+ * stream order: the solve starts after earlier work on it and later work
+ * starts after the solve.
  */
 fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi,
                             void *const *E);

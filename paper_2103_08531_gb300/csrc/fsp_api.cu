@@ -425,19 +425,20 @@ int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, f
 }
 
 // One pass over many items: the items sharing a padded length go in one launch.
+// Launches of the same stage (pass) are independent of each other.
 struct PassLaunch {
-    int kind, axis, N, flag;
+    int kind, axis, N, flag, stage;
     std::vector<PassArgs> items;
 };
 
 static void group_pass(std::vector<PassLaunch> &out, int kind, int axis, int flag, const std::vector<PassArgs> &items,
-                       const std::vector<int> &Ns, const std::vector<int> &use)
+                       const std::vector<int> &Ns, const std::vector<int> &use, int stage)
 {
     std::vector<int> seen;
     for (size_t i = 0; i < items.size(); ++i) {
         if (!use[i] || std::find(seen.begin(), seen.end(), Ns[i]) != seen.end()) continue;
         seen.push_back(Ns[i]);
-        PassLaunch L{kind, axis, Ns[i], flag, {}};
+        PassLaunch L{kind, axis, Ns[i], flag, stage, {}};
         for (size_t k = i; k < items.size(); ++k)
             if (use[k] && Ns[k] == Ns[i]) L.items.push_back(items[k]);
         out.push_back(std::move(L));
@@ -458,23 +459,57 @@ static std::vector<PassLaunch> batch_launches(const std::vector<const Plan *> &p
         is3[i] = plans[i]->three_d;
     }
     std::vector<PassLaunch> L;
-    group_pass(L, PASS_P1F, 0, 0, items, N0, all);
-    group_pass(L, PASS_P2F, 1, 0, items, N1, is3);
-    group_pass(L, PASS_P3F, 2, withE, items, N2, all);
-    group_pass(L, PASS_P4F, 1, withE, items, N1, is3);
-    group_pass(L, PASS_P5F, 0, 0, items, N0, all);
+    group_pass(L, PASS_P1F, 0, 0, items, N0, all, 0);
+    group_pass(L, PASS_P2F, 1, 0, items, N1, is3, 1);
+    group_pass(L, PASS_P3F, 2, withE, items, N2, all, 2);
+    group_pass(L, PASS_P4F, 1, withE, items, N1, is3, 3);
+    group_pass(L, PASS_P5F, 0, 0, items, N0, all, 4);
     return L;
 }
 
-static int run_launches(const std::vector<PassLaunch> &L, cudaStream_t st)
+static int launch_one(const PassLaunch &x, cudaStream_t st)
 {
-    for (const PassLaunch &x : L) {
-        const int n = (int)x.items.size();
-        const int var = tuned_variant(x.kind, x.N);
-        int e = x.axis == 0 ? launch_axis0(x.kind, x.N, x.items.data(), n, var, st)
-                : x.axis == 1 ? launch_axis1(x.kind, x.N, x.items.data(), n, x.flag, var, st)
-                              : launch_axis2(x.kind, x.N, x.items.data(), n, x.flag, var, st);
-        if (e) return FSP_ERR_CUDA;
+    const int n = (int)x.items.size();
+    const int var = tuned_variant(x.kind, x.N);
+    const int e = x.axis == 0 ? launch_axis0(x.kind, x.N, x.items.data(), n, var, st)
+                  : x.axis == 1 ? launch_axis1(x.kind, x.N, x.items.data(), n, x.flag, var, st)
+                                : launch_axis2(x.kind, x.N, x.items.data(), n, x.flag, var, st);
+    return e ? FSP_ERR_CUDA : FSP_OK;
+}
+
+// Streams and events that let the launches of one stage run side by side:
+// the first launch of a stage goes on the caller's stream, the k-th on aux[k-1],
+// forked from and joined back into the caller's stream by events (in a
+// captured graph, parallel branches).
+struct Fork {
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+};
+
+static int run_launches(const std::vector<PassLaunch> &L, cudaStream_t st, const Fork *fk = nullptr)
+{
+    size_t i = 0;
+    while (i < L.size()) {
+        size_t end = i + 1;
+        while (end < L.size() && L[end].stage == L[i].stage) ++end;
+        const size_t width = end - i;
+        if (!fk || width == 1 || fk->aux.size() + 1 < width) {
+            for (; i < end; ++i)
+                if (launch_one(L[i], st)) return FSP_ERR_CUDA;
+            continue;
+        }
+        if (cudaEventRecord(fk->fork, st) != cudaSuccess) return FSP_ERR_CUDA;
+        for (size_t k = 1; k < width; ++k) {
+            cudaStream_t s = fk->aux[k - 1];
+            if (cudaStreamWaitEvent(s, fk->fork, 0) != cudaSuccess || launch_one(L[i + k], s) ||
+                cudaEventRecord(fk->join[k - 1], s) != cudaSuccess)
+                return FSP_ERR_CUDA;
+        }
+        if (launch_one(L[i], st)) return FSP_ERR_CUDA;
+        for (size_t k = 1; k < width; ++k)
+            if (cudaStreamWaitEvent(st, fk->join[k - 1], 0) != cudaSuccess) return FSP_ERR_CUDA;
+        i = end;
     }
     return FSP_OK;
 }
@@ -512,7 +547,37 @@ struct DirectJob {
 struct fsp_batch {
     std::vector<PassLaunch> launches;
     std::vector<DirectJob> direct;
+    Fork fork;   // prebuilt batches run the launches of a stage side by side
+    ~fsp_batch()
+    {
+        for (cudaStream_t s : fork.aux) cudaStreamDestroy(s);
+        for (cudaEvent_t e : fork.join) cudaEventDestroy(e);
+        if (fork.fork) cudaEventDestroy(fork.fork);
+    }
 };
+
+// Streams for the widest stage of a prebuilt batch (set-up, not a solve).
+static int make_fork(fsp_batch &b)
+{
+    size_t widest = 1;
+    for (size_t i = 0; i < b.launches.size();) {
+        size_t end = i + 1;
+        while (end < b.launches.size() && b.launches[end].stage == b.launches[i].stage) ++end;
+        widest = std::max(widest, end - i);
+        i = end;
+    }
+    if (widest == 1) return FSP_OK;
+    if (cudaEventCreateWithFlags(&b.fork.fork, cudaEventDisableTiming) != cudaSuccess) return FSP_ERR_CUDA;
+    for (size_t k = 1; k < widest; ++k) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FSP_ERR_CUDA;
+        b.fork.aux.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return FSP_ERR_CUDA;
+        b.fork.join.push_back(e);
+    }
+    return FSP_OK;
+}
 
 static int check_batch(fsp_plan *const *plans, int count, const void *const *rho, void *const *phi, void *const *E)
 {
@@ -550,7 +615,7 @@ static void plan_batch(fsp_batch &b, fsp_plan *const *plans, int count, const vo
 
 static int run_batch(const fsp_batch &b, cudaStream_t st)
 {
-    int rc = run_launches(b.launches, st);
+    int rc = run_launches(b.launches, st, b.fork.aux.empty() ? nullptr : &b.fork);
     for (size_t i = 0; i < b.direct.size() && rc == FSP_OK; ++i) {
         const DirectJob &d = b.direct[i];
         rc = run_direct_forward(*d.p, d.p->ws, d.rho, d.phi, d.E, st);
@@ -582,6 +647,12 @@ extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const 
         return nullptr;
     }
     plan_batch(*b, plans, count, rho, phi, E);
+    rc = make_fork(*b);
+    if (rc) {
+        delete b;
+        set_err(rc);
+        return nullptr;
+    }
     set_err(FSP_OK);
     return b;
 }

@@ -26,8 +26,13 @@ int supported_axis2(int N)
 
 template <int N, int MAXI>
 struct Occ2 {
-    static inline int p3 = 1, p3a = 1, p3one = 1;
+    static inline int p3 = 1, p3a = 1, p3one = 1, wide = 1;
 };
+
+// Lines of 1024 and 2048 points: the multi-warp-per-line middle pass
+// (p3_fwd_wide) unless variant bit 4 asks for the block kernel.
+template <int N>
+constexpr bool kWide = N == 1024 || N == 2048;
 
 template <int N, int MAXI>
 static int prep_one()
@@ -55,6 +60,13 @@ static int prep_one()
         e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd_blk<N, MAXI>, C::THREADS, C::SMEM_STAGED);
         Occ2<N, MAXI>::p3 = std::max(1, b);
         e |= cudaFuncSetAttribute(p3_adj_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if constexpr (kWide<N>) {
+            using W = WideCfg<N>;
+            int bw = 0;
+            e |= cudaFuncSetAttribute(p3_fwd_wide<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::SMEM);
+            e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, p3_fwd_wide<N, MAXI>, W::THREADS, W::SMEM);
+            Occ2<N, MAXI>::wide = std::max(1, bw);
+        }
     }
     return e;
 }
@@ -84,9 +96,27 @@ static int units_p3(const PassArgs &a)
 }
 
 template <int N>
+static int units_wide(const PassArgs &a)
+{
+    if constexpr (kWide<N>) return ((a.n0 + 1) * a.rows1 + WideCfg<N>::LPC - 1) / WideCfg<N>::LPC;
+    else return 0;
+}
+
+template <int N>
 static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     const int cap_sm = sm_count();
+    if constexpr (kWide<N>) {
+        if (kind == PASS_P3F && !(var & 4)) {
+            return chunked(items, n, units_wide<N>, [&](auto &w) {
+                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+                const int total = w.offs[w.nitems];
+                const int grid = std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::wide));
+                return launch_pdl_if(kLongPdl<N>, p3_fwd_wide<N, MAXI>, grid, WideCfg<N>::THREADS, WideCfg<N>::SMEM,
+                                     st, w, flag);
+            });
+        }
+    }
     return chunked(items, n, units_p3<N>, [&](auto &w) {
         constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
         const int total = w.offs[w.nitems];

@@ -245,7 +245,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // ------------------------------------------------------------------- passes
 
-enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
+// Sync group of a transform: the whole block, one warp, or (SYNC_LINE0 + w) the
+// w warps of one line, with named barrier 1 + threadIdx.x / (32 w).
+enum { SYNC_BLOCK = 0, SYNC_WARP = 1, SYNC_LINE0 = 64 };
 // Twiddle sources: TW_TABLE loads each W^(r m) from the table (cheap when the
 // lanes of a warp share m, as in column tiles); TW_POW loads W^m, W^2m, W^4m,
 // W^8m and forms the other powers by products (lanes with distinct m).
@@ -261,7 +263,9 @@ enum { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 // TW_GALL: gathered blocks [r][k] for every pass with NS > 1 (not only NS < 32),
 // read from global memory: a warp's 16-32 consecutive k read consecutive
 // entries (the long-line passes, whose tables do not fit in shared memory).
-enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4, TW_QSMEM = 5, TW_GALL = 7 };
+// TW_GSMEM: the TW_GALL blocks copied into shared memory, passed without the
+// main table in front (entry [pass][r][k] at tw + OFF + r NS + k).
+enum { TW_TABLE = 0, TW_POW = 1, TW_GATHER = 2, TW_SMEM = 3, TW_STABLE = 4, TW_QSMEM = 5, TW_GALL = 7, TW_GSMEM = 8 };
 
 // W_N^m (m < N) from the quarter table.
 template <int N>
@@ -278,15 +282,21 @@ __device__ __forceinline__ float2 qtw(const float2 *tq, int m)
 template <int TW>
 __device__ __forceinline__ float2 ldtw(const float2 *p)
 {
-    if constexpr (TW == TW_SMEM || TW == TW_STABLE) return *p;
+    if constexpr (TW == TW_SMEM || TW == TW_STABLE || TW == TW_GSMEM) return *p;
     else return __ldg(p);
 }
 
 template <int SYNC>
 __device__ __forceinline__ void lsync()
 {
-    if constexpr (SYNC == SYNC_WARP) __syncwarp();
-    else __syncthreads();
+    if constexpr (SYNC == SYNC_WARP) {
+        __syncwarp();
+    } else if constexpr (SYNC > SYNC_LINE0) {
+        constexpr int LT = 32 * (SYNC - SYNC_LINE0);
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / LT), "n"(LT) : "memory");
+    } else {
+        __syncthreads();
+    }
 }
 
 // u[r] *= W^(r m) (conjugated for the inverse), r = 1 .. R-1.
@@ -343,7 +353,8 @@ struct NextOffAll {
 };
 template <int TW, int NS, int R, int OFF>
 struct NextOffT {
-    static constexpr int value = TW == TW_GALL ? NextOffAll<NS, R, OFF>::value : NextOff<NS, R, OFF>::value;
+    static constexpr int value =
+        (TW == TW_GALL || TW == TW_GSMEM) ? NextOffAll<NS, R, OFF>::value : NextOff<NS, R, OFF>::value;
 };
 
 // Twiddles of butterfly column k (= b mod NS) in a pass with (NS, R); OFF is
@@ -354,6 +365,9 @@ __device__ __forceinline__ void pass_twiddles(float2 *u, const float2 *__restric
     if constexpr (TW == TW_GALL) {
 #pragma unroll
         for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], __ldg(tw + N + OFF + r * NS + k));
+    } else if constexpr (TW == TW_GSMEM) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul_dir<INV>(u[r], tw[OFF + r * NS + k]);
     } else if constexpr (TW == TW_QSMEM) {
         static_assert(N % 4 == 0, "the quarter table needs N divisible by 4");
         const int m = k * (N / (NS * R));

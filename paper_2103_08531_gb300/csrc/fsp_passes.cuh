@@ -1515,6 +1515,104 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     }
 }
 
+// Forward middle pass for 1024- and 2048-point lines (2 n2 = 1024, 2048):
+// 16 values per thread, a line spread over N / 512 warps that synchronise
+// among themselves only (a named barrier per line), four warps per CTA,
+// persistent over line groups with the next line's input prefetched into
+// registers, as the warp-per-line pass does for shorter lines.  Twiddles: the
+// all-pass gathered blocks copied into shared memory (consecutive lanes read
+// consecutive entries in every pass).  Exchange lines padded one slot per 16
+// (conflict-free for these radix plans: bank simulation on the host).
+template <int N>
+struct WideCfg {
+    static constexpr int E = Plan1D<N>::E;
+    using RAD = typename Plan1D<N>::R;
+    static constexpr int T = N / E;
+    static_assert(T % 32 == 0 && T <= 128, "a line is one to four whole warps");
+    static constexpr int WPL = T / 32;            // warps per line
+    static constexpr int WARPS = 4;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int LPC = WARPS / WPL;       // lines per CTA
+    static constexpr int PAD = 4;
+    static constexpr int SPAN = RowSpan<N, PAD>::value;
+    static constexpr int TWG = AuxEndAll<1, 0, RAD>::value;   // gathered twiddle entries
+    static constexpr size_t SMEM = (size_t)(LPC * SPAN + TWG) * sizeof(float2);
+    static constexpr int SYNC = LPC == 1 ? SYNC_BLOCK : SYNC_LINE0 + WPL;
+};
+
+template <int N, int MAXI>
+__global__ void __launch_bounds__(WideCfg<N>::THREADS) p3_fwd_wide(const __grid_constant__ Work<MAXI> W, int withE)
+{
+    using C = WideCfg<N>;
+    constexpr int E = C::E, T = C::T, LPC = C::LPC;
+    constexpr int n2 = N / 2;   // every item of a length-N launch has n2 = N / 2
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    pdl_trigger();
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const int nw = W.count();
+    RowView<C::PAD> sm{smem + li * C::SPAN};
+    float2 *stw = smem + LPC * C::SPAN;
+    {
+        const float2 *gtw = W.item[0].tw2 + N;   // the gathered blocks follow the N-entry table
+        for (int i = threadIdx.x; i < C::TWG; i += C::THREADS) stw[i] = gtw[i];
+    }
+    __syncthreads();
+    pdl_wait();
+    float2 pv[E / 2];   // the next line's pruned input
+    auto fetch = [&](int gg) {
+        const int it = W.find(gg < nw ? gg : 0);
+        const PassArgs &b = W.item[it];
+        const int bline = (gg - W.offs[it]) * LPC + li;
+        const bool bact = gg < nw && bline < (b.n0 + 1) * b.rows1;
+        const float2 *L = b.buf0 + (size_t)(bact ? bline : 0) * n2;
+#pragma unroll
+        for (int r = 0; r < E / 2; ++r)
+            if (bact) pv[r] = L[j + r * T];
+    };
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) pv[r] = make_float2(0.f, 0.f);
+    int g = blockIdx.x;
+    fetch(g);
+    for (; g < nw; g += gridDim.x) {
+        FSP_UNIT(W, g, a, u);
+        const int lines = (a.n0 + 1) * a.rows1;
+        const int line = u * LPC + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
+        fetch(g + gridDim.x);
+        const int kx = lc / a.rows1, row = lc % a.rows1;
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, C::SYNC, TW_GSMEM>(v, j, stw, sm);
+        const float *Kr = krow(a, kx, row);
+        float2 q[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = j + r * T;
+            const int kf = k <= n2 ? k : N - k;
+            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+            const float kk = wave(k, n2, a.k2s);
+            q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
+        }
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, C::SYNC, TW_GSMEM>(v, j, stw, sm);
+        if (act) {
+            float2 *L0 = a.buf0 + (size_t)lc * n2;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
+        }
+        if (withE) {
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, C::SYNC, TW_GSMEM>(q, j, stw, sm);
+            if (act) {
+                float2 *L1 = a.buf1 + (size_t)lc * n2;
+#pragma unroll
+                for (int r = 0; r < E / 2; ++r) L1[j + r * T] = q[r];
+            }
+        }
+    }
+}
+
 // Adjoint middle pass, warp per line group.
 template <int N, int MAXI>
 __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_constant__ Work<MAXI> W, int hasE)

@@ -108,7 +108,10 @@ def test_solve_parity(fsp, oracle_mod, method, name, shape, h):
 
 
 LONG = [
-    ("z1024", (32, 32, 512), (0.03, 0.03, 0.004), "vgf"),     # middle pass on 1024-point lines
+    ("z1024", (32, 32, 512), (0.03, 0.03, 0.004), "vgf"),     # middle pass on 1024-point lines (two warps a line)
+    ("z1024he", (64, 32, 512), (0.02, 0.03, 0.004), "he"),
+    ("y1024", (96, 512), (0.01, 0.002), "vgf"),                # 2D, 1024-point middle lines
+    ("y2048", (64, 1024), (0.01, 0.001), "vgf"),               # 2D, 2048-point middle lines (four warps a line)
     ("y4096", (64, 2048), (0.01, 0.001), "he"),                # 2D, 4096-point middle lines
     ("y8192", (32, 4096), (0.02, 0.0005), "he"),               # 2D, 8192-point middle lines
     ("x4096", (2048, 64), (0.001, 0.01), "he"),                # 2D, 4096-point column tiles (narrow)
@@ -236,7 +239,8 @@ def test_autograd_matches_fd_and_oracle_gradient(fsp, oracle_mod):
 
 def test_batched_equals_single(fsp):
     shapes = [((32, 32, 32), (0.02, 0.03, 0.025)), ((64, 32, 32), (0.01, 0.02, 0.03)),
-              ((32, 64, 96), (0.03, 0.01, 0.02)), ((32, 32, 128), (0.02, 0.02, 0.005))]
+              ((32, 64, 96), (0.03, 0.01, 0.02)), ((32, 32, 128), (0.02, 0.02, 0.005)),
+              ((32, 32, 512), (0.02, 0.02, 0.004)), ((64, 32, 512), (0.03, 0.02, 0.004))]
     plans, rhos = [], []
     for i, (s, h) in enumerate(shapes):
         plans.append(fsp.Plan(s, h, "vgf"))
@@ -338,7 +342,7 @@ def _write_cache(path, arch, shape, var_tile, var_p3):
 
 @pytest.mark.parametrize("shape,h", [((64, 64, 32), (0.02, 0.025, 0.03)), ((32, 128, 64), (0.03, 0.01, 0.02)),
                                      ((128, 64), (0.01, 0.02)), ((32, 64, 128), (0.03, 0.02, 0.01)),
-                                     ((32, 32, 256), (0.03, 0.02, 0.005))])
+                                     ((32, 32, 256), (0.03, 0.02, 0.005)), ((32, 32, 512), (0.03, 0.02, 0.004))])
 def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     """Each launch variant the autotuner can pick gives the oracle's answer."""
     cap = torch.cuda.get_device_capability()
@@ -353,7 +357,8 @@ def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     try:
         # column tiles: 0 TMA-staged group tiles, 2 the same one CTA per SM, 4 / 5 the cp.async
         # block tiles with 16 / 8 values per thread, 6 / 7 those one CTA per SM
-        for vt, vp in [(0, 0), (2, 2), (4, 0), (5, 0), (6, 2), (7, 2)]:
+        # middle pass (bits 2 and, at 2n = 1024 / 2048, 4): the same bits of vt
+        for vt, vp in [(0, 0), (2, 2), (4, 4), (5, 4), (6, 6), (7, 6)]:
             _write_cache(path, arch, shape, vt, vp)
             plan.autotune(path, 0)
             assert fsp.tuned_variant("p1_fwd", 2 * shape[0]) == vt
