@@ -236,6 +236,19 @@ int fsp_host_pipe_solve(fsp_host_pipe *pipe, int count, const void *const *rho_h
 void fsp_host_pipe_destroy(fsp_host_pipe *pipe);
 
 /*
+ * Schedule of single 3D solves: with planes > 0 the three middle passes (axis
+ * 1 forward, axis 2 forward-multiply-inverse, axis 1 inverse) run in turn on
+ * groups of `planes` k0 planes of the half spectrum instead of each over all
+ * n0 + 1 planes, so that one group's intermediates (about 2.5 MB per plane at
+ * 256^3) can stay in the 129 MB L2 from one pass to the next; 0 (the default)
+ * turns it off.  It applies where those passes are the single-solve kernels
+ * with plane ranges (2 n_y, 2 n_z <= 512, TMA column tiles); elsewhere it is
+ * ignored.  Results are the same bit for bit.  Not a step of the paper's
+ * method: a memory-traffic schedule for the same arithmetic.
+ */
+int fsp_plan_set_plane_group(fsp_plan *plan, int planes);
+
+/*
  * Device-side status of the plan's solves: FSP_OK, or FSP_ERR_TIMEOUT if a
  * kernel's bounded wait (the shared-memory tile barriers of the TMA-staged
  * passes, which give up after about 2 s) failed in some solve since the last

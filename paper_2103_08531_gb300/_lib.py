@@ -46,6 +46,7 @@ SIGNATURES = {
     "fsp_host_pipe_solve": (_i, [_vp, _i, _vpp, _vpp, _vpp, _vp]),
     "fsp_host_pipe_destroy": (None, [_vp]),
     "fsp_plan_device_status": (_i, [_vp, _i]),
+    "fsp_plan_set_plane_group": (_i, [_vp, _i]),
 }
 
 

@@ -296,6 +296,13 @@ extern "C" int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int
     return set_err(FSP_OK);
 }
 
+extern "C" int fsp_plan_set_plane_group(fsp_plan *plan, int planes)
+{
+    if (!plan || planes < 0) return set_err(FSP_ERR_INVALID);
+    plan->p.plane_group = planes;
+    return set_err(FSP_OK);
+}
+
 extern "C" int fsp_plan_device_status(fsp_plan *plan, int clear)
 {
     if (!plan || !plan->p.status) return set_err(FSP_ERR_INVALID);
@@ -335,6 +342,8 @@ static PassArgs base_args(const Plan &p, void *ws)
     a.tw2 = p.tw2;
     a.K = p.K;
     a.status = p.status;
+    a.kx0 = 0;
+    a.kxn = p.n0 + 1;
     a.buf0 = reinterpret_cast<float2 *>(ws);
     a.buf1 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + align_up(p.buf_elems * sizeof(float2), 256));
     return a;
@@ -363,6 +372,16 @@ static PassArgs fwd_args(const Plan &p, void *ws, const float *rho, float *phi, 
     return a;
 }
 
+// Plane groups (3D): P2, P3 and P4 run group by group over the k0 planes, so
+// that a group's intermediates can stay in L2 between the three passes.  Only
+// where those passes are the single-solve kernels that take a plane range
+// (TMA column tiles, warp-per-line middle pass: 2 n1, 2 n2 <= 512).
+static bool plane_groups_apply(const Plan &p)
+{
+    return p.three_d && p.plane_group > 0 && p.plane_group < p.n0 + 1 && 2 * p.n1 <= 512 && 2 * p.n2 <= 512 &&
+           !(tuned_variant(PASS_P2F, 2 * p.n1) & 4) && !(tuned_variant(PASS_P4F, 2 * p.n1) & 4);
+}
+
 // Forward pipeline for one plan on its workspace `ws`.
 int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
 {
@@ -371,6 +390,26 @@ int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E,
     const int withE = E != nullptr;
     const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
     int e = 0, m = 0;
+    if (plane_groups_apply(p)) {
+        // pass events: before P1, after P1, then after the grouped P2-P4, after P5
+        mark(p, m++, st);
+        e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
+        mark(p, m++, st);
+        for (int k = 0; k <= p.n0 && !e; k += p.plane_group) {
+            PassArgs g = a;
+            g.kx0 = k;
+            g.kxn = std::min(p.plane_group, p.n0 + 1 - k);
+            e = launch_axis1(PASS_P2F, N1, &g, 1, 0, tuned_variant(PASS_P2F, N1), st);
+            if (!e) e = launch_axis2(PASS_P3F, N2, &g, 1, withE, tuned_variant(PASS_P3F, N2), st);
+            if (!e) e = launch_axis1(PASS_P4F, N1, &g, 1, withE, tuned_variant(PASS_P4F, N1), st);
+        }
+        mark(p, m++, st);
+        mark(p, m++, st);
+        mark(p, m++, st);
+        if (!e) e = launch_axis0(PASS_P5F, N0, &a, 1, tuned_variant(PASS_P5F, N0), st);
+        mark(p, m++, st);
+        return e ? FSP_ERR_CUDA : FSP_OK;
+    }
     mark(p, m++, st);
     e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
     mark(p, m++, st);

@@ -112,7 +112,7 @@ static int tma_launch1(int kind, const PassArgs &a, int flag, int var, cudaStrea
     std::memset(&m, 0, sizeof(m));
     const unsigned long long dims[2] = {(unsigned long long)a.n2, (unsigned long long)(a.n0 + 1) * a.rows1};
     const unsigned long long str[1] = {(unsigned long long)a.n2 * 8};
-    const int units = (a.n0 + 1) * (a.n2 / 16);
+    const int units = a.kxn * (a.n2 / 16);
     const int sms = sm_count();
     if (kind == PASS_P2F) {
         const unsigned box[2] = {16, N / 2};

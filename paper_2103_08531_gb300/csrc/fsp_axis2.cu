@@ -90,7 +90,7 @@ int prepare_axis2(int N)
 template <int N>
 static int units_p3(const PassArgs &a)
 {
-    const int lines = (a.n0 + 1) * a.rows1;
+    const int lines = a.kxn * a.rows1;   // kxn = n0 + 1 except in plane-grouped single solves (p3_fwd1)
     if constexpr (N <= 512) return (lines + WarpCfg<N>::LPW - 1) / WarpCfg<N>::LPW;   // warp-level units
     else return (lines + RowCfg<N>::LPC - 1) / RowCfg<N>::LPC;
 }

@@ -39,6 +39,7 @@ struct Plan {
     double2 *dtw[3];          // FP64 twiddles exp(2 pi i m / (2 n_a)) per pass axis (direct plans)
     double kd[3];             // 2 pi / (2 n_a h_a) per pass axis, FP64
     int *status;              // device status word (FSP_OK, or FSP_ERR_TIMEOUT from a bounded wait)
+    int plane_group;          // > 0: P2-P4 of single 3D solves run in groups of this many k0 planes
 };
 
 // fsp_precompute.cu

@@ -246,12 +246,12 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_c
     pdl_trigger();
     const TmaSmem s = tma_smem<N>(smem_raw, 1, NH);
     const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 16, units = (a.n0 + 1) * zt;
+    const int zt = a.n2 / 16, units = a.kxn * zt;   // planes [kx0, kx0 + kxn)
     tma_bar_setup(s.bar);
     const float2 *tw = C::twiddles(s.ex, a.tw1);
     auto issue = [&](int w) {
         mbar_expect_tx(s.bar, NH * 128);
-        tma_load_2d(s.stage[0], &maps.m[0], (w % zt) * 16, (w / zt) * a.rows1, s.bar);
+        tma_load_2d(s.stage[0], &maps.m[0], (w % zt) * 16, (a.kx0 + w / zt) * a.rows1, s.bar);
     };
     pdl_wait();
     int w = blockIdx.x;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_c
     const ColView sm{s.ex + col, 16};
     for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
         const bool ok = mbar_wait(s.bar, ph);
-        const int kx = w / zt, z = (w % zt) * 16 + col;
+        const int kx = a.kx0 + w / zt, z = (w % zt) * 16 + col;
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
@@ -289,12 +289,12 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_c
     pdl_trigger();
     const TmaSmem s = tma_smem<N>(smem_raw, 2, N);
     const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 16, units = (a.n0 + 1) * zt;
+    const int zt = a.n2 / 16, units = a.kxn * zt;   // planes [kx0, kx0 + kxn)
     tma_bar_setup(s.bar);
     const float2 *tw = C::twiddles(s.ex, a.tw1);
     auto issue = [&](int w) {
         mbar_expect_tx(s.bar, (withE ? 2 : 1) * N * 128);
-        const int x = (w % zt) * 16, y = (w / zt) * a.rows1;
+        const int x = (w % zt) * 16, y = (a.kx0 + w / zt) * a.rows1;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             tma_load_2d(s.stage[0] + b * BOXR * 16, &maps.m[0], x, y + b * BOXR, s.bar);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_c
     const int n1 = a.n1;
     for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
         const bool ok = mbar_wait(s.bar, ph);
-        const int kx = w / zt, z = (w % zt) * 16 + col;
+        const int kx = a.kx0 + w / zt, z = (w % zt) * 16 + col;
         float2 v[E], q[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {

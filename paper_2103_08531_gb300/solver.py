@@ -97,6 +97,14 @@ class Plan:
                    "fsp_plan_kernel_spectrum")
         return out
 
+    def set_plane_group(self, planes: int):
+        """Run the middle passes of single 3D solves in groups of `planes` k0 planes (0: off)."""
+        _lib.check(self.lib.fsp_plan_set_plane_group(self.handle, int(planes)), "fsp_plan_set_plane_group")
+
+    def device_status(self, clear: bool = True) -> int:
+        """Device-side status of earlier solves (0, or 6 = FSP_ERR_TIMEOUT); synchronises."""
+        return int(self.lib.fsp_plan_device_status(self.handle, int(clear)))
+
     def set_pass_events(self, events):
         """Record the given torch.cuda.Event objects at the pass boundaries of later solves (None: off)."""
         if not events:

@@ -391,6 +391,27 @@ def test_autotune_measures_and_writes_cache(fsp, tmp_path):
     plan.autotune(path, 0)
 
 
+# ------------------------------------------------------------ plane groups
+
+@pytest.mark.parametrize("shape,h,groups", [((64, 64, 64), (0.02, 0.02, 0.02), (1, 5, 16, 64)),
+                                            ((96, 128, 256), (0.01, 0.015, 0.007), (7, 32))])
+def test_plane_groups_give_the_same_bits(fsp, shape, h, groups):
+    """The middle passes run group by group over the k0 planes: identical results, clean status."""
+    plan = fsp.Plan(shape, h, "vgf")
+    rho = torch.from_numpy(_mixture(shape, h, seed=91).rho(np.float32)).cuda()
+    phi0, E0 = plan.solve(rho)
+    phi_only0, _ = plan.solve(rho, with_E=False)
+    for g in groups:
+        plan.set_plane_group(g)
+        phi, E = plan.solve(rho)
+        ph1, _ = plan.solve(rho, with_E=False)
+        torch.cuda.synchronize()
+        assert torch.equal(phi, phi0) and torch.equal(E, E0), g
+        assert torch.equal(ph1, phi_only0), g
+    plan.set_plane_group(0)
+    assert plan.device_status() == 0
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("direct", [False, True])
