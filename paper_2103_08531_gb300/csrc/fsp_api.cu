@@ -142,7 +142,9 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
     p.kd[1] = dim == 3 ? 2.0 * pi / (2.0 * ny * hy) : 0.0;
     p.kd[2] = 2.0 * pi / (2.0 * p.n2 * hh2);
     p.dtype = dtype;
-    const bool fast = supported_axis0(2 * p.n0) && supported_axis2(2 * p.n2) && (p.n2 % 2 == 0) &&
+    // the column tiles of the first and last passes take 32 reals (16 complex)
+    // of the contiguous axis at a time
+    const bool fast = supported_axis0(2 * p.n0) && supported_axis2(2 * p.n2) && (p.n2 % 32 == 0) &&
                       (dim == 2 || (supported_axis1(2 * p.n1) && 2 * p.n0 <= 1024 && 2 * p.n2 <= 1024));
     p.direct = dtype == FSP_F64 || (flags & FSP_PLAN_DIRECT) || !fast;
     if (p.direct && (p.n0 > DIRECT_MAX_N || p.n2 > DIRECT_MAX_N || (dim == 3 && p.n1 > DIRECT_MAX_N))) {

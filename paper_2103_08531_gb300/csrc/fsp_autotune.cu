@@ -28,7 +28,7 @@ using namespace fsp;
 
 namespace {
 
-const int kLengths[] = {64, 128, 192, 256, 512, 1024, 2048, 4096, 8192};
+const int kLengths[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 2048, 4096, 8192};
 constexpr int kNL = sizeof(kLengths) / sizeof(kLengths[0]);
 const char *kKindName[PASS_KINDS] = {"p1_fwd", "p1_adj", "p2_fwd", "p2_adj", "p3_fwd", "p3_adj", "p4_fwd", "p5_fwd"};
 
@@ -45,7 +45,7 @@ int length_index(int N)
 std::vector<int> candidates(int kind, int N)
 {
     const bool tile = kind == PASS_P1F || kind == PASS_P2F || kind == PASS_P4F || kind == PASS_P5F;
-    if (N > 512) return (kind == PASS_P3F && (N == 1024 || N == 2048)) ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0};
+    if (N > 512) return (kind == PASS_P3F && (N == 768 || N == 1024 || N == 2048)) ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0};
     if (tile) return N == 192 ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0, 2, 4, 5, 6, 7};
     if (kind == PASS_P3F || kind == PASS_P3A) return {0, 2};
     return {0};

@@ -9,7 +9,7 @@
 
 namespace fsp {
 
-#define FSP_AXIS0_SIZES(X) X(64) X(128) X(192) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+#define FSP_AXIS0_SIZES(X) X(32) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(2048) X(4096) X(8192)
 
 int supported_axis0(int N)
 {

@@ -9,7 +9,7 @@
 
 namespace fsp {
 
-#define FSP_AXIS1_SIZES(X) X(64) X(128) X(192) X(256) X(512) X(1024)
+#define FSP_AXIS1_SIZES(X) X(32) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
 
 int supported_axis1(int N)
 {

@@ -598,12 +598,15 @@ __global__ void k_twiddles_aux(float2 *tw)
 // Radix plans per padded length for block-synchronous tiles (E values per thread).
 template <int N>
 struct Plan1D;
+template <> struct Plan1D<32> { static constexpr int E = 8; using R = Radices<8, 4>; };
 template <> struct Plan1D<64> { static constexpr int E = 8; using R = Radices<8, 8>; };
 template <> struct Plan1D<96> { static constexpr int E = 12; using R = Radices<4, 4, 2, 3>; };
 template <> struct Plan1D<128> { static constexpr int E = 8; using R = Radices<8, 8, 2>; };
 template <> struct Plan1D<192> { static constexpr int E = 12; using R = Radices<4, 4, 4, 3>; };
 template <> struct Plan1D<256> { static constexpr int E = 8; using R = Radices<8, 8, 4>; };
+template <> struct Plan1D<384> { static constexpr int E = 12; using R = Radices<4, 4, 4, 2, 3>; };
 template <> struct Plan1D<512> { static constexpr int E = 8; using R = Radices<8, 8, 8>; };
+template <> struct Plan1D<768> { static constexpr int E = 12; using R = Radices<4, 4, 4, 4, 3>; };
 template <> struct Plan1D<1024> { static constexpr int E = 16; using R = Radices<16, 8, 8>; };
 template <> struct Plan1D<2048> { static constexpr int E = 16; using R = Radices<16, 16, 8>; };
 template <> struct Plan1D<4096> { static constexpr int E = 16; using R = Radices<16, 16, 16>; };
@@ -612,10 +615,13 @@ template <> struct Plan1D<8192> { static constexpr int E = 16; using R = Radices
 // Radix plans for 16-values-per-thread work (one warp or less per line).
 template <int N>
 struct Plan16;
+template <> struct Plan16<32> { static constexpr int E = 8; using R = Radices<8, 4>; };
 template <> struct Plan16<64> { static constexpr int E = 8; using R = Radices<8, 8>; };
+template <> struct Plan16<96> { static constexpr int E = 12; using R = Radices<4, 4, 2, 3>; };
 template <> struct Plan16<128> { static constexpr int E = 16; using R = Radices<16, 8>; };
 template <> struct Plan16<192> { static constexpr int E = 12; using R = Radices<4, 4, 4, 3>; };
 template <> struct Plan16<256> { static constexpr int E = 16; using R = Radices<16, 16>; };
+template <> struct Plan16<384> { static constexpr int E = 12; using R = Radices<4, 4, 4, 2, 3>; };
 template <> struct Plan16<512> { static constexpr int E = 16; using R = Radices<16, 16, 2>; };
 
 
