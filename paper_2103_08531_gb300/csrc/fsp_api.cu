@@ -113,7 +113,7 @@ extern "C" fsp_plan *fsp_plan_create_ex(int nx, int ny, int nz, double hx, doubl
         set_err(FSP_ERR_INVALID);
         return nullptr;
     }
-    fsp_plan *handle = new (std::nothrow) fsp_plan();
+    fsp_plan *handle = inject_fault("alloc") ? nullptr : new (std::nothrow) fsp_plan();
     if (!handle) {
         set_err(FSP_ERR_NOMEM);
         return nullptr;
@@ -387,6 +387,7 @@ static bool plane_groups_apply(const Plan &p)
 // Forward pipeline for one plan on its workspace `ws`.
 int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
 {
+    Range range(p.direct ? "fsp solve (direct sums)" : "fsp solve");
     if (p.direct) return run_direct_forward(p, ws, rho, phi, E, st);   // buffers in the plan's precision
     PassArgs a = fwd_args(p, ws, rho, phi, E);
     const int withE = E != nullptr;
@@ -413,25 +414,37 @@ int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E,
         return e ? FSP_ERR_CUDA : FSP_OK;
     }
     mark(p, m++, st);
-    e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
+    {
+        Range r("P1 axis 0 pad + R2C");
+        e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
+    }
     mark(p, m++, st);
     if (!e && p.three_d) {
+        Range r("P2 axis 1 forward");
         e = launch_axis1(PASS_P2F, N1, &a, 1, 0, tuned_variant(PASS_P2F, N1), st);
         mark(p, m++, st);
     }
-    if (!e) e = launch_axis2(PASS_P3F, N2, &a, 1, withE, tuned_variant(PASS_P3F, N2), st);
+    if (!e) {
+        Range r("P3 axis 2 forward, kernel product, inverse");
+        e = launch_axis2(PASS_P3F, N2, &a, 1, withE, tuned_variant(PASS_P3F, N2), st);
+    }
     mark(p, m++, st);
     if (!e && p.three_d) {
+        Range r("P4 axis 1 inverse + crop");
         e = launch_axis1(PASS_P4F, N1, &a, 1, withE, tuned_variant(PASS_P4F, N1), st);
         mark(p, m++, st);
     }
-    if (!e) e = launch_axis0(PASS_P5F, N0, &a, 1, tuned_variant(PASS_P5F, N0), st);
+    if (!e) {
+        Range r("P5 axis 0 C2R + crop");
+        e = launch_axis0(PASS_P5F, N0, &a, 1, tuned_variant(PASS_P5F, N0), st);
+    }
     mark(p, m++, st);
     return e ? FSP_ERR_CUDA : FSP_OK;
 }
 
 int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, float *g_rho, cudaStream_t st)
 {
+    Range range("fsp adjoint");
     if (p.direct) return run_direct_adjoint(p, ws, g_phi, g_E, g_rho, st);
     if (!g_E) return run_forward(p, ws, g_phi, g_rho, nullptr, st);   // A is symmetric
     PassArgs a = base_args(p, ws);
@@ -656,6 +669,7 @@ static void plan_batch(fsp_batch &b, fsp_plan *const *plans, int count, const vo
 
 static int run_batch(const fsp_batch &b, cudaStream_t st)
 {
+    Range range("fsp batch");
     int rc = run_launches(b.launches, st, b.fork.aux.empty() ? nullptr : &b.fork);
     for (size_t i = 0; i < b.direct.size() && rc == FSP_OK; ++i) {
         const DirectJob &d = b.direct[i];
@@ -682,7 +696,7 @@ extern "C" fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const 
         set_err(rc);
         return nullptr;
     }
-    fsp_batch *b = new (std::nothrow) fsp_batch();
+    fsp_batch *b = inject_fault("alloc") ? nullptr : new (std::nothrow) fsp_batch();
     if (!b) {
         set_err(FSP_ERR_NOMEM);
         return nullptr;

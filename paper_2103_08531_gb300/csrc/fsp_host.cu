@@ -46,7 +46,7 @@ extern "C" fsp_host_pipe *fsp_host_pipe_create(fsp_plan *plan, int depth, int wi
         fsp::record_error(FSP_ERR_INVALID);
         return nullptr;
     }
-    fsp_host_pipe *p = new (std::nothrow) fsp_host_pipe();
+    fsp_host_pipe *p = fsp::inject_fault("alloc") ? nullptr : new (std::nothrow) fsp_host_pipe();
     if (!p) {
         fsp::record_error(FSP_ERR_NOMEM);
         return nullptr;

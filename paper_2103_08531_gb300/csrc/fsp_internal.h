@@ -4,7 +4,10 @@
 #include "../../include/fsp.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
 
 struct fsp_plan;
 
@@ -95,6 +98,25 @@ int record_error(int s);
 // 4 or 8.  Returns 0 or a CUresult.
 int encode_tensor_map(void *map, const void *base, int rank, int elem_bytes, const unsigned long long *dims,
                       const unsigned long long *strides, const unsigned *box);
+
+// NVTX range around a solve or a pass (host-side enqueue; shown by Nsight tools,
+// free when no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
+// Host-side fault injection for tests of the error paths: when the
+// environment variable FSP_FAULT_INJECT names `what` ("alloc": the
+// allocations of plan, batch and host-pipe creation), the call fails as if
+// the allocation had failed.  Nothing on the GPU is involved.
+inline bool inject_fault(const char *what)
+{
+    const char *v = getenv("FSP_FAULT_INJECT");
+    return v && strcmp(v, what) == 0;
+}
 
 // fsp_autotune.cu: the variant chosen for a pass kind at padded length N (0 if untuned)
 int tuned_variant(int kind, int N);

@@ -43,13 +43,36 @@ struct PassArgs {
                       // p4_tma); every other pass covers all n0 + 1 planes
 };
 
+// FSP_DEBUG_BOUNDS (a debug build, see build.py): every intermediate and grid
+// index is checked against its buffer's extent; an index outside it records
+// FSP_ERR_INVALID in the solve's status word (fsp_plan_device_status) and the
+// access goes to element 0 instead, so a bad index is reported without a
+// fault.  Release builds compile the plain index arithmetic.
+#ifdef FSP_DEBUG_BOUNDS
+__device__ __forceinline__ size_t checked_index(const PassArgs &a, bool ok, size_t i)
+{
+    if (ok) return i;
+    if (a.status) atomicCAS(a.status, 0, 1 /* FSP_ERR_INVALID */);
+    return 0;
+}
+#endif
 __device__ __forceinline__ size_t iidx(const PassArgs &a, int k0, int row, int z)
 {
-    return ((size_t)k0 * a.rows1 + row) * a.n2 + z;
+    const size_t i = ((size_t)k0 * a.rows1 + row) * a.n2 + z;
+#ifdef FSP_DEBUG_BOUNDS
+    return checked_index(a, k0 >= 0 && k0 <= a.n0 && row >= 0 && row < a.rows1 && z >= 0 && z < a.n2, i);
+#else
+    return i;
+#endif
 }
 __device__ __forceinline__ size_t gidx(const PassArgs &a, int x, int y, int z)
 {
-    return ((size_t)x * a.n1 + y) * a.n2 + z;
+    const size_t i = ((size_t)x * a.n1 + y) * a.n2 + z;
+#ifdef FSP_DEBUG_BOUNDS
+    return checked_index(a, x >= 0 && x < a.n0 && y >= 0 && y < a.n1 && z >= 0 && z < a.n2, i);
+#else
+    return i;
+#endif
 }
 
 // Signed wavenumber index of position k on a padded axis of n cells: m in

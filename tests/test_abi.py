@@ -104,3 +104,16 @@ def test_python_package_has_no_cpu_fallback():
             text = open(os.path.join(src_dir, fn)).read()
             assert "oracle" not in text.replace("oracle_", ""), fn
             assert "torch.fft" not in text, fn
+
+
+def test_fault_injection_fails_creation_on_the_host(lib, monkeypatch):
+    """FSP_FAULT_INJECT=alloc makes plan creation fail as an allocation failure (FSP_ERR_NOMEM),
+    before any GPU call; unset, the same arguments reach the device step."""
+    monkeypatch.setenv("FSP_FAULT_INJECT", "alloc")
+    assert lib.fsp_plan_create(32, 32, 32, 0.1, 0.1, 0.1, 1, 0) is None
+    assert lib.fsp_last_error() == 4
+    assert lib.fsp_plan_create_ex(64, 64, 0, 0.1, 0.1, 0.0, 0, 0, 1.0, float("nan"), 0) is None
+    assert lib.fsp_last_error() == 4
+    monkeypatch.setenv("FSP_FAULT_INJECT", "other")
+    lib.fsp_plan_create(-1, 1, 1, 0.1, 0.1, 0.1, 0, 0)
+    assert lib.fsp_last_error() == 1   # argument checks still come first

@@ -210,3 +210,45 @@ def test_direct_plan_rejects_pass_events(fsp):
         e.record()
     with pytest.raises(fsp.FspError):
         plan.set_pass_events(evs)
+
+
+_DEBUG_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_2103_08531_gb300 import _lib, build
+_lib.load(build.DEBUG_LIB)                      # every call below goes to the bounds-checked build
+import paper_2103_08531_gb300 as fsp
+import oracle, workloads as W
+worst = 0.0
+for shape, h in (((32, 64, 96), (0.03, 0.02, 0.011)), ((64, 128), (0.02, 0.011)), ((16, 48, 192), (0.05, 0.03, 0.01)),
+                 ((13, 17, 11), (0.05, 0.04, 0.06))):
+    prob = W.Problem("d", shape, h, [(np.zeros(len(shape)), np.array([0.1 * n * x for n, x in zip(shape, h)]), 1.0)])
+    rho32 = prob.rho(np.float32)
+    plan = fsp.Plan(shape, h, "vgf")
+    phi, E = plan.solve(torch.from_numpy(rho32).cuda())
+    g = plan.adjoint(phi, E)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0, shape
+    k = oracle.kernel_vgf(list(shape), h)
+    p_ref, E_ref = oracle.solve_with_kernel(k, rho32.astype(np.float64), h)
+    worst = max(worst, float(np.max(np.abs(phi.cpu().numpy() - p_ref)) / np.max(np.abs(p_ref))))
+print("ok", worst)
+"""
+
+
+@pytest.mark.slow
+def test_debug_bounds_build_reports_no_bad_index(fsp):
+    """The FSP_DEBUG_BOUNDS build (every intermediate and grid index checked against its buffer)
+    runs solves and adjoints of 3D, 2D, new-length and direct-path plans with a clean device
+    status and the oracle's answer; it runs in a child process that loads only that build."""
+    import os
+    import subprocess
+    import sys
+    from paper_2103_08531_gb300 import build
+    build.build(debug_bounds=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", _DEBUG_SCRIPT.format(root=root)], capture_output=True, text=True,
+                         timeout=600)
+    assert res.returncode == 0, res.stderr[-3000:]
+    assert res.stdout.startswith("ok")
+    assert float(res.stdout.split()[1]) <= 1e-5
