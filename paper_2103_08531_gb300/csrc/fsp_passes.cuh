@@ -1485,7 +1485,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int li = lane / T, j = lane % T;
     const int lines = a.kxn * a.rows1;       // lines of planes [kx0, kx0 + kxn)
-    const size_t line0 = (size_t)a.kx0 * a.rows1;
+    const int line0 = a.kx0 * a.rows1;
     const int groups = (lines + LPW - 1) / LPW;
     const int gstride = gridDim.x * C::WARPS;
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
@@ -1496,7 +1496,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     auto fetch = [&](int gg) {
         const int line = gg * LPW + li;
         const bool act = gg < groups && line < lines;
-        const float2 *L = a.buf0 + (line0 + (act ? line : 0)) * n2;
+        const float2 *L = a.buf0 + (size_t)(line0 + (act ? line : 0)) * n2;
 #pragma unroll
         for (int r = 0; r < E / 2; ++r)
             if (act) pv[r] = L[j + r * T];
@@ -1507,12 +1507,12 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     for (; g < groups; g += gstride) {
         const int line = g * LPW + li;
         const bool act = line < lines;
-        const int lc = act ? line : 0;
+        const int lc = line0 + (act ? line : 0);   // absolute line index
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
         fetch(g + gstride);
-        const int kx = (int)((line0 + lc) / a.rows1), row = (int)((line0 + lc) % a.rows1);
+        const int kx = lc / a.rows1, row = lc % a.rows1;
         line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         const float *Kr = krow(a, kx, row);
         float2 u[E];
@@ -1526,14 +1526,14 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
         }
         line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         if (act) {
-            float2 *L0 = a.buf0 + (line0 + lc) * n2;
+            float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
         }
         if (withE) {
             line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, tw, sm);
             if (act) {
-                float2 *L1 = a.buf1 + (line0 + lc) * n2;
+                float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll
                 for (int r = 0; r < E / 2; ++r) L1[j + r * T] = u[r];
             }

@@ -133,6 +133,8 @@ MIXED_LENGTHS = [
 def _runs_fft_passes(plan):
     """Plans on the direct-sum path refuse pass events; the FFT-pass plans take them."""
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(plan.passes + 1)]
+    for e in evs:
+        e.record()   # torch creates the CUDA event on its first record
     try:
         plan.set_pass_events(evs)
     except Exception:
