@@ -425,6 +425,7 @@ def run_gpu(args):
         t = time.perf_counter()
         plans[m] = fsp.Plan(prob.shape, prob.h, m)
         plan_s[m] = time.perf_counter() - t
+    tuning = load_tuning(plans["vgf"], prob.shape)
     phi = torch.empty_like(rho)
     E = torch.empty((3,) + prob.shape, dtype=torch.float32, device=rho.device)
     stream = torch.cuda.current_stream()
@@ -548,6 +549,7 @@ def run_gpu(args):
                                device_sms(local), *alu_clock(clk)),
         "gpu_launches": npass * args.steps,
         "clocks": clk,
+        "tuning": tuning,
     }
     if e2e_ms is not None:
         line["e2e"] = {"value": ws * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
@@ -606,6 +608,21 @@ def alu_clock(clk):
     return 2070.0, "nominal maximum SM clock (no clock samples)"
 
 
+def load_tuning(plan, shape):
+    """Read the committed launch-variant cache (written by paper_2103_08531_gb300.tune on this GPU
+    type) into the process-wide table; report the variants the plan's passes now use."""
+    from paper_2103_08531_gb300 import tune as T
+    import paper_2103_08531_gb300 as fsp
+    have = os.path.exists(T.TUNE_CACHE)
+    if have:
+        plan.autotune(T.TUNE_CACHE, 0)
+    lengths = {"p1_fwd": 2 * shape[0], "p3_fwd": 2 * shape[-1], "p5_fwd": 2 * shape[0]}
+    if len(shape) == 3:
+        lengths.update({"p2_fwd": 2 * shape[1], "p4_fwd": 2 * shape[1]})
+    return {"cache": os.path.relpath(T.TUNE_CACHE, ROOT) if have else None,
+            "variants": {f"{k}/{N}": fsp.tuned_variant(k, N) for k, N in sorted(lengths.items())}}
+
+
 def _timed(fn, steps, warmup):
     import torch
     for _ in range(warmup):
@@ -635,6 +652,7 @@ def run_other(args):
         t = time.perf_counter()
         plans = [fsp.Plan(p.shape, p.h, "vgf") for p in probs]
         t_plan = time.perf_counter() - t
+        line["tuning"] = load_tuning(plans[0], probs[0].shape)
         rhos = [torch.from_numpy(p.rho(np.float32)).cuda() for p in probs]
         batch = fsp.Batch(plans, rhos)
         graph = batch.capture()
@@ -666,6 +684,7 @@ def run_other(args):
             t = time.perf_counter()
             plan = fsp.Plan(prob.shape, prob.h, m)
             plan_s[m] = time.perf_counter() - t
+            line["tuning"] = load_tuning(plan, prob.shape)
             phi = torch.empty_like(rho)
             E = torch.empty((2,) + prob.shape, device="cuda")
             res[m] = _timed(lambda: plan.solve(rho, phi=phi, E=E), args.steps, args.warmup) / args.steps
@@ -697,6 +716,7 @@ def run_other(args):
         n, B = 128, 8
         probs, target = W.training_batch(n, B)
         plan = fsp.Plan((n, n, n), probs[0].h, "vgf")
+        line["tuning"] = load_tuning(plan, (n, n, n))
         tgt = torch.from_numpy(target).cuda()
         rhos = [torch.from_numpy(p.rho(np.float32)).cuda().requires_grad_(True) for p in probs]
 

@@ -521,10 +521,13 @@ static std::vector<PassLaunch> batch_launches(const std::vector<const Plan *> &p
     return L;
 }
 
+// Batched launches keep the default variants: the tuning table is timed on
+// single solves (whose column passes are the TMA-staged tiles) and does not
+// carry over to the batched kernels.
 static int launch_one(const PassLaunch &x, cudaStream_t st)
 {
     const int n = (int)x.items.size();
-    const int var = tuned_variant(x.kind, x.N);
+    const int var = n == 1 ? tuned_variant(x.kind, x.N) : 0;
     const int e = x.axis == 0 ? launch_axis0(x.kind, x.N, x.items.data(), n, var, st)
                   : x.axis == 1 ? launch_axis1(x.kind, x.N, x.items.data(), n, x.flag, var, st)
                                 : launch_axis2(x.kind, x.N, x.items.data(), n, x.flag, var, st);

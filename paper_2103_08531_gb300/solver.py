@@ -69,7 +69,9 @@ class Plan:
                        "fsp_plan_set_workspace")
             mode = os.environ.get("FSP_AUTOTUNE", "off")
             if mode in ("cached", "full", "retune"):
-                self.autotune(os.environ.get("FSP_TUNE_CACHE"), {"cached": 0, "full": 1, "retune": 2}[mode])
+                cache = os.environ.get("FSP_TUNE_CACHE") or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                                        "tune_cache.json")
+                self.autotune(cache, {"cached": 0, "full": 1, "retune": 2}[mode])
 
     def autotune(self, cache_path=None, mode: int = 1):
         """Pick launch variants for this plan's passes (see fsp_autotune in include/fsp.h)."""
