@@ -1549,6 +1549,11 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
 // all-pass gathered blocks copied into shared memory (consecutive lanes read
 // consecutive entries in every pass).  Exchange lines padded one slot per 16
 // (conflict-free for these radix plans: bank simulation on the host).
+// Resident CTAs the register allocation of p3_fwd_wide is sized for (3: 168
+// registers, 12 warps per SM; 4: 128 registers with a small spill, 16 warps).
+#ifndef FSP_WIDE_MINB
+#define FSP_WIDE_MINB 3
+#endif
 template <int N>
 struct WideCfg {
     static constexpr int E = Plan1D<N>::E;
@@ -1567,7 +1572,7 @@ struct WideCfg {
 };
 
 template <int N, int MAXI>
-__global__ void __launch_bounds__(WideCfg<N>::THREADS) p3_fwd_wide(const __grid_constant__ Work<MAXI> W, int withE)
+__global__ void __launch_bounds__(WideCfg<N>::THREADS, FSP_WIDE_MINB) p3_fwd_wide(const __grid_constant__ Work<MAXI> W, int withE)
 {
     using C = WideCfg<N>;
     constexpr int E = C::E, T = C::T, LPC = C::LPC;
