@@ -259,6 +259,17 @@ int fsp_plan_set_plane_group(fsp_plan *plan, int planes);
 int fsp_plan_device_status(fsp_plan *plan, int clear);
 
 /*
+ * Test hook for the bounded device waits: runs one small kernel whose wait on
+ * a shared-memory barrier can never complete (a transaction count that no
+ * copy fills; no copy is in flight) with a limit of limit_seconds (0 < limit
+ * <= 10), and returns the status that kernel recorded: FSP_ERR_TIMEOUT when
+ * the wait gave up as it should; FSP_ERR_INVALID for a bad limit,
+ * FSP_ERR_CUDA if a CUDA call failed.  Synchronises the device.  The same
+ * bounded wait guards every tile of the TMA-staged passes (about 2 s there).
+ */
+int fsp_selftest_wait_timeout(double limit_seconds);
+
+/*
  * Test hook: copy the plan's FP32 kernel spectrum to host memory, layout
  * [nx+1][ny+1][nz+1] (2D: [nx+1][ny+1]), entry (kx,ky,kz) = prod(h)/prod(2n)
  * times the DFT of the padded kernel at index k (indices k and 2n-k share it).

@@ -47,6 +47,7 @@ SIGNATURES = {
     "fsp_host_pipe_destroy": (None, [_vp]),
     "fsp_plan_device_status": (_i, [_vp, _i]),
     "fsp_plan_set_plane_group": (_i, [_vp, _i]),
+    "fsp_selftest_wait_timeout": (_i, [_d]),
 }
 
 

@@ -69,13 +69,13 @@ __device__ __forceinline__ unsigned long long globaltimer()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for the phase with the given parity to complete, at most kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+// Wait for the phase with the given parity to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     return true;
 }
 // Order this thread's earlier shared-memory accesses (generic proxy) before

@@ -79,6 +79,7 @@ def test_null_arguments(lib):
     assert lib.fsp_solve_noalloc(None, None, None, None, None) == 1
     assert lib.fsp_gradient_fd(None, None, None, None) == 1
     assert lib.fsp_autotune(None, None, 0) == 1
+    assert lib.fsp_selftest_wait_timeout(-1.0) == 1
     # every entry point leaves its status in fsp_last_error()
     lib.fsp_plan_create_ex(32, 32, 32, 0.1, 0.1, 0.1, 1, 0, 1.0, float("nan"), 2)
     assert lib.fsp_last_error() == 1

@@ -455,6 +455,28 @@ def test_plane_groups_give_the_same_bits(fsp, shape, h, groups):
     assert plan.device_status() == 0
 
 
+# ------------------------------------------------------- bounded device waits
+
+def test_device_wait_gives_up_and_the_context_stays_usable(fsp):
+    """A shared-memory barrier wait that can never complete gives up after its limit, records
+    FSP_ERR_TIMEOUT and returns; solves on the same context still give the right answer."""
+    import time
+    lib = fsp.load()
+    t = time.perf_counter()
+    assert lib.fsp_selftest_wait_timeout(0.05) == 6   # FSP_ERR_TIMEOUT
+    assert time.perf_counter() - t < 5.0
+    assert lib.fsp_last_error() == 6
+    assert lib.fsp_selftest_wait_timeout(0.0) == 1
+    shape, h = (32, 32, 32), (2 / 32,) * 3
+    plan = fsp.Plan(shape, h, "vgf")
+    rho = torch.from_numpy(_mixture(shape, h, seed=3).rho(np.float32)).cuda()
+    phi, E = plan.solve(rho)
+    phi2, E2 = plan.solve(rho)
+    torch.cuda.synchronize()
+    assert torch.equal(phi, phi2) and torch.isfinite(E).all()
+    assert plan.device_status() == 0
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("direct", [False, True])
