@@ -1,8 +1,8 @@
 // fsp_autotune.cu -- picks a launch variant per (pass, padded length) by timing.
 //
-// Variants (bits): 4 = the cp.async block-synchronous column tiles of
-// P1/P2/P4/P5 instead of the TMA-staged group tiles (single solves, lengths
-// <= 512); 1 = with bit 4, 8 values per thread in those tiles instead of 16
+// Variants (bits): 4 = the cp.async column tiles of P1/P2/P4/P5 instead of
+// the TMA-staged ones (lengths <= 512; single solves: batches keep the
+// defaults); 1 = with bit 4, 8 values per thread in those tiles instead of 16
 // (not 192); 2 = one CTA per SM in the persistent launches instead of as many
 // as fit.  For the middle pass at 2n = 1024 and 2048, bit 4 selects the
 // block-synchronous line kernel instead of the multi-warp-per-line one.  The

@@ -82,8 +82,8 @@ static int prep_one()
     return e;
 }
 
-// TMA-staged group tiles (single solves, 2n <= 512)
-template <int N>
+// TMA-staged column tiles (2n <= 512), single solves (MAXI = 1) and batches
+template <int N, int MAXI>
 struct TmaOcc0 {
     static inline int p1 = 1, p5 = 1;
 };
@@ -91,18 +91,19 @@ template <int N>
 static constexpr size_t smem_p1_tma() { return TmaTile<N>::smem(1, N / 2); }
 template <int N>
 static constexpr size_t smem_p5_tma() { return TmaTile<N>::smem(3, N / 2); }
+static_assert(sizeof(Work<BATCH_MAX>) + sizeof(TmaBatch<BATCH_MAX>) + 16 <= 32764, "kernel parameters too large");
 
-template <int N>
+template <int N, int MAXI>
 static int prep_tma()
 {
     int e = 0, b1 = 0, b5 = 0;
     using C = TileCfg<N, 16>;
-    e |= cudaFuncSetAttribute(p1_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1_tma<N>());
-    e |= cudaFuncSetAttribute(p5_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_tma<N>, C::THREADS, smem_p1_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_tma<N>, C::THREADS, smem_p5_tma<N>());
-    TmaOcc0<N>::p1 = std::max(1, b1);
-    TmaOcc0<N>::p5 = std::max(1, b5);
+    e |= cudaFuncSetAttribute(p1_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1_tma<N>());
+    e |= cudaFuncSetAttribute(p5_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_tma<N, MAXI>, C::THREADS, smem_p1_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_tma<N, MAXI>, C::THREADS, smem_p5_tma<N>());
+    TmaOcc0<N, MAXI>::p1 = std::max(1, b1);
+    TmaOcc0<N, MAXI>::p5 = std::max(1, b5);
     return e;
 }
 
@@ -110,37 +111,49 @@ template <int N>
 static int prep()
 {
     int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
-    if constexpr (N <= 512) e |= prep_tma<N>();
+    if constexpr (N <= 512) e |= prep_tma<N, 1>() | prep_tma<N, BATCH_MAX>();
     return e;
 }
 
-// The TMA-staged P1 / P5 of one solve (maps built here from the solve's buffers).
 template <int N>
-static int tma_launch0(int kind, const PassArgs &a, int var, cudaStream_t st)
+static int units_p1_tma(const PassArgs &a) { return a.n1 * (a.n2 / 32); }
+template <int N>
+static int units_p5_tma(const PassArgs &a) { return a.n1 * (a.n2 / 16); }
+
+// The TMA-staged P1 / P5 of one launch's items: tensor maps of every item
+// built here from its own buffers.
+template <int N, class Wk>
+static int tma_launch0(int kind, const Wk &w, int var, cudaStream_t st)
 {
+    constexpr int MAXI = Wk::max_items;
     using C = TileCfg<N, 16>;
-    TmaMaps m;
+    TmaBatch<MAXI> m;
     std::memset(&m, 0, sizeof(m));
-    const int sms = sm_count();
-    if (kind == PASS_P1F) {
-        const unsigned long long dims[3] = {(unsigned long long)a.n2, (unsigned long long)a.n1,
-                                            (unsigned long long)a.n0};
-        const unsigned long long str[2] = {(unsigned long long)a.n2 * 4, (unsigned long long)a.n1 * a.n2 * 4};
-        const unsigned box[3] = {32, 1, N / 2};
-        if (encode_tensor_map(&m.m[0], a.in[0], 3, 4, dims, str, box)) return (int)cudaErrorInvalidValue;
-        const int units = a.n1 * (a.n2 / 32);
-        const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc0<N>::p1));
-        return launch_pdl(p1_tma<N>, grid, C::THREADS, smem_p1_tma<N>(), st, a, m);
+    for (int i = 0; i < w.nitems; ++i) {
+        const PassArgs &a = w.item[i];
+        if (kind == PASS_P1F) {
+            const unsigned long long dims[3] = {(unsigned long long)a.n2, (unsigned long long)a.n1,
+                                                (unsigned long long)a.n0};
+            const unsigned long long str[2] = {(unsigned long long)a.n2 * 4, (unsigned long long)a.n1 * a.n2 * 4};
+            const unsigned box[3] = {32, 1, N / 2};
+            if (encode_tensor_map(&m.m[i][0], a.in[0], 3, 4, dims, str, box)) return (int)cudaErrorInvalidValue;
+        } else {
+            const unsigned long long dims[3] = {(unsigned long long)a.n2, (unsigned long long)a.rows1,
+                                                (unsigned long long)a.n0 + 1};
+            const unsigned long long str[2] = {(unsigned long long)a.n2 * 8, (unsigned long long)a.rows1 * a.n2 * 8};
+            const unsigned box[3] = {16, 1, N / 2};
+            if (encode_tensor_map(&m.m[i][0], a.buf0, 3, 8, dims, str, box) ||
+                encode_tensor_map(&m.m[i][1], a.buf1, 3, 8, dims, str, box))
+                return (int)cudaErrorInvalidValue;
+        }
     }
-    const unsigned long long dims[3] = {(unsigned long long)a.n2, (unsigned long long)a.rows1,
-                                        (unsigned long long)a.n0 + 1};
-    const unsigned long long str[2] = {(unsigned long long)a.n2 * 8, (unsigned long long)a.rows1 * a.n2 * 8};
-    const unsigned box[3] = {16, 1, N / 2};
-    if (encode_tensor_map(&m.m[0], a.buf0, 3, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
-    if (encode_tensor_map(&m.m[1], a.buf1, 3, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
-    const int units = a.n1 * (a.n2 / 16);
-    const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc0<N>::p5));
-    return launch_pdl(p5_tma<N>, grid, C::THREADS, smem_p5_tma<N>(), st, a, m);
+    const int total = w.offs[w.nitems];
+    const int sms = sm_count();
+    if (kind == PASS_P1F)
+        return launch_pdl(p1_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc0<N, MAXI>::p1)), C::THREADS,
+                          smem_p1_tma<N>(), st, w, m);
+    return launch_pdl(p5_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc0<N, MAXI>::p5)), C::THREADS,
+                      smem_p5_tma<N>(), st, w, m);
 }
 
 int prepare_axis0(int N)
@@ -204,8 +217,13 @@ template <int N>
 static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
 {
     if constexpr (N <= 512) {
-        if ((kind == PASS_P1F || kind == PASS_P5F) && n == 1 && !(var & 4) && items[0].n2 % 32 == 0)
-            return tma_launch0<N>(kind, items[0], var, st);
+        if ((kind == PASS_P1F || kind == PASS_P5F) && !(var & 4)) {
+            bool fits = true;   // the TMA tiles take 32 reals (16 complex) of the contiguous axis at a time
+            for (int i = 0; i < n; ++i) fits = fits && items[i].n2 % 32 == 0;
+            if (fits)
+                return chunked(items, n, kind == PASS_P1F ? units_p1_tma<N> : units_p5_tma<N>,
+                               [&](auto &w) { return tma_launch0<N>(kind, w, var, st); });
+        }
     }
     if (kind == PASS_P1F || kind == PASS_P5F) {
         return chunked(items, n, kind == PASS_P1F ? units_p1f<N> : units_p5f<N>, [&](auto &w) {

@@ -70,8 +70,8 @@ static int prep_one()
     return e;
 }
 
-// TMA-staged group tiles (single solves, 2n <= 512)
-template <int N>
+// TMA-staged column tiles (2n <= 512), single solves (MAXI = 1) and batches
+template <int N, int MAXI>
 struct TmaOcc1 {
     static inline int p2 = 1, p4 = 1;
 };
@@ -80,17 +80,17 @@ static constexpr size_t smem_p2_tma() { return TmaTile<N>::smem(1, N / 2); }
 template <int N>
 static constexpr size_t smem_p4_tma() { return TmaTile<N>::smem(2, N); }
 
-template <int N>
+template <int N, int MAXI>
 static int prep_tma()
 {
     int e = 0, b2 = 0, b4 = 0;
     using C = TileCfg<N, 16>;
-    e |= cudaFuncSetAttribute(p2_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2_tma<N>());
-    e |= cudaFuncSetAttribute(p4_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_tma<N>, C::THREADS, smem_p2_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_tma<N>, C::THREADS, smem_p4_tma<N>());
-    TmaOcc1<N>::p2 = std::max(1, b2);
-    TmaOcc1<N>::p4 = std::max(1, b4);
+    e |= cudaFuncSetAttribute(p2_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2_tma<N>());
+    e |= cudaFuncSetAttribute(p4_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_tma<N, MAXI>, C::THREADS, smem_p2_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_tma<N, MAXI>, C::THREADS, smem_p4_tma<N>());
+    TmaOcc1<N, MAXI>::p2 = std::max(1, b2);
+    TmaOcc1<N, MAXI>::p4 = std::max(1, b4);
     return e;
 }
 
@@ -98,33 +98,44 @@ template <int N>
 static int prep()
 {
     int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
-    if constexpr (N <= 512) e |= prep_tma<N>();
+    if constexpr (N <= 512) e |= prep_tma<N, 1>() | prep_tma<N, BATCH_MAX>();
     return e;
 }
 
-// The TMA-staged P2 / P4 of one solve: maps over buf1 (P2) or buf0 and buf1
-// (P4) as [(n0 + 1) rows1][n2] complex.
+// (k0, 16-column tile) units over planes [kx0, kx0 + kxn)
 template <int N>
-static int tma_launch1(int kind, const PassArgs &a, int flag, int var, cudaStream_t st)
+static int units_tma1(const PassArgs &a) { return a.kxn * (a.n2 / 16); }
+
+// The TMA-staged P2 / P4 of one launch's items: maps over each item's buf1
+// (P2) or buf0 and buf1 (P4) as [(n0 + 1) rows1][n2] complex.
+template <int N, class Wk>
+static int tma_launch1(int kind, const Wk &w, int flag, int var, cudaStream_t st)
 {
+    constexpr int MAXI = Wk::max_items;
     using C = TileCfg<N, 16>;
-    TmaMaps m;
+    TmaBatch<MAXI> m;
     std::memset(&m, 0, sizeof(m));
-    const unsigned long long dims[2] = {(unsigned long long)a.n2, (unsigned long long)(a.n0 + 1) * a.rows1};
-    const unsigned long long str[1] = {(unsigned long long)a.n2 * 8};
-    const int units = a.kxn * (a.n2 / 16);
-    const int sms = sm_count();
-    if (kind == PASS_P2F) {
-        const unsigned box[2] = {16, N / 2};
-        if (encode_tensor_map(&m.m[0], a.buf1, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
-        const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc1<N>::p2));
-        return launch_pdl(p2_tma<N>, grid, C::THREADS, smem_p2_tma<N>(), st, a, m);
+    for (int i = 0; i < w.nitems; ++i) {
+        const PassArgs &a = w.item[i];
+        const unsigned long long dims[2] = {(unsigned long long)a.n2, (unsigned long long)(a.n0 + 1) * a.rows1};
+        const unsigned long long str[1] = {(unsigned long long)a.n2 * 8};
+        if (kind == PASS_P2F) {
+            const unsigned box[2] = {16, N / 2};
+            if (encode_tensor_map(&m.m[i][0], a.buf1, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
+        } else {
+            const unsigned box[2] = {16, N < 256 ? N : 256};
+            if (encode_tensor_map(&m.m[i][0], a.buf0, 2, 8, dims, str, box) ||
+                encode_tensor_map(&m.m[i][1], a.buf1, 2, 8, dims, str, box))
+                return (int)cudaErrorInvalidValue;
+        }
     }
-    const unsigned box[2] = {16, N < 256 ? N : 256};
-    if (encode_tensor_map(&m.m[0], a.buf0, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
-    if (encode_tensor_map(&m.m[1], a.buf1, 2, 8, dims, str, box)) return (int)cudaErrorInvalidValue;
-    const int grid = std::min(units, sms * ((var & 2) ? 1 : TmaOcc1<N>::p4));
-    return launch_pdl(p4_tma<N>, grid, C::THREADS, smem_p4_tma<N>(), st, a, m, flag);
+    const int total = w.offs[w.nitems];
+    const int sms = sm_count();
+    if (kind == PASS_P2F)
+        return launch_pdl(p2_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc1<N, MAXI>::p2)), C::THREADS,
+                          smem_p2_tma<N>(), st, w, m);
+    return launch_pdl(p4_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc1<N, MAXI>::p4)), C::THREADS,
+                      smem_p4_tma<N>(), st, w, m, flag);
 }
 
 int prepare_axis1(int N)
@@ -170,8 +181,12 @@ template <int N>
 static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     if constexpr (N <= 512) {
-        if ((kind == PASS_P2F || kind == PASS_P4F) && n == 1 && !(var & 4) && items[0].n2 % 16 == 0)
-            return tma_launch1<N>(kind, items[0], flag, var, st);
+        if ((kind == PASS_P2F || kind == PASS_P4F) && !(var & 4)) {
+            bool fits = true;
+            for (int i = 0; i < n; ++i) fits = fits && items[i].n2 % 16 == 0;
+            if (fits)
+                return chunked(items, n, units_tma1<N>, [&](auto &w) { return tma_launch1<N>(kind, w, flag, var, st); });
+        }
     }
     if (kind == PASS_P2F || kind == PASS_P4F) {
         return chunked(items, n, units_tile<N>, [&](auto &w) {

@@ -73,8 +73,9 @@ int prepare_axis2(int N);
 // var: tuning variant bits (1 = 8 values per thread in column tiles, 2 = one
 // CTA per SM in persistent launches, 4 = the cp.async block-synchronous column
 // tiles instead of the TMA-staged group tiles); chosen by the autotuner
-// (fsp_autotune.cu).  Single solves of 2n <= 512 run the TMA-staged column
-// passes unless bit 4 is set; batches and longer columns run the others.
+// (fsp_autotune.cu).  Column passes of 2n <= 512 run the TMA-staged tiles
+// (single solves and batches) unless bit 4 is set; longer columns run the
+// block and staged long-column kernels.
 int launch_axis0(int kind, int N, const PassArgs *items, int n, int var, cudaStream_t st);
 int launch_axis1(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);
 int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st);

@@ -28,11 +28,6 @@
 
 namespace fsp {
 
-// Tensor maps passed by value as __grid_constant__ kernel parameters.
-struct TmaMaps {
-    CUtensorMap m[2];
-};
-
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -167,19 +162,26 @@ __device__ __forceinline__ bool tma_tile_failed(bool ok, uint64_t *bar, unsigned
 
 // ------------------------------------------------------------------ kernels
 //
-// Persistent over tiles (grid <= tiles).  Each mirrors the arithmetic and the
+// Persistent over tiles (grid <= tiles) of up to MAXI independent solves (a
+// Work list, as the other batched passes; MAXI = 1 for one solve), each item
+// with its own tensor maps.  Each kernel mirrors the arithmetic and the
 // thread mapping of its cp.async counterpart in fsp_passes.cuh (p1_fwd,
 // p2_fwd, p4_fwd, p5_fwd: column = tid % 16, line thread j = tid / 16,
 // block-synchronous transforms through the [position][16] exchange buffer);
 // only the staging differs.  After the block barrier that ends the reads of a
 // stage, thread 0 issues the next tile's copies into it.
 
+template <int MAXI>
+struct TmaBatch {
+    CUtensorMap m[MAXI][2];
+};
+
 // P1: rho column pairs (z, z + 1) of a tile of 32 reals -> half spectrum in
 // k0, rows 0 .. n1 - 1 of buf1 (3D) or buf0 (2D).  Unit: (y, tile).  Map 0:
 // rho as [n0][n1][n2] floats, box 32 x 1 x N/2.
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_constant__ PassArgs a,
-                                                                  const __grid_constant__ TmaMaps maps)
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_constant__ Work<MAXI> W,
+                                                                  const __grid_constant__ TmaBatch<MAXI> maps)
 {
     using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
@@ -188,26 +190,30 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_c
     pdl_trigger();
     const TmaSmem s = tma_smem<N>(smem_raw, 1, NH);
     const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 32, units = a.n1 * zt;
+    const int nw = W.count();
     tma_bar_setup(s.bar);
-    const float2 *tw = C::twiddles(s.ex, a.tw0);   // (its block barrier also publishes the mbarrier)
+    const float2 *tw = C::twiddles(s.ex, W.item[0].tw0);   // (its block barrier also publishes the mbarrier)
     auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const int zt = b.n2 / 32;
         mbar_expect_tx(s.bar, NH * 128);
-        tma_load_3d(s.stage[0], &maps.m[0], (w % zt) * 32, w / zt, 0, s.bar);
+        tma_load_3d(s.stage[0], &maps.m[it_ub][0], (ub % zt) * 32, ub / zt, 0, s.bar);
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (tid == 0 && w < units) issue(w);
+    if (tid == 0 && w < nw) issue(w);
     const ColView sm{s.ex + col, 16};
-    float2 *__restrict__ dst = a.three_d ? a.buf1 : a.buf0;
-    for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
+    for (unsigned ph = 0; w < nw; w += gridDim.x, ph ^= 1) {
         const bool ok = mbar_wait(s.bar, ph);
-        const int y = w / zt, z0 = (w % zt) * 32 + 2 * col;
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / 32;
+        const int y = u / zt, z0 = (u % zt) * 32 + 2 * col;
+        float2 *__restrict__ dst = a.three_d ? a.buf1 : a.buf0;
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
         if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
-        if (tid == 0 && w + (int)gridDim.x < units) {
+        if (tid == 0 && w + (int)gridDim.x < nw) {
             fence_proxy_async();
             issue(w + gridDim.x);
         }
@@ -234,10 +240,11 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_c
 }
 
 // P2: buf1 rows 0 .. n1 - 1 -> forward axis 1 -> buf0 rows 0 .. 2 n1 - 1.
-// Unit: (k0, tile).  Map 0: buf1 as [(n0 + 1) rows1][n2] complex, box 16 x N/2.
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_constant__ PassArgs a,
-                                                                  const __grid_constant__ TmaMaps maps)
+// Unit: (k0, tile) over planes [kx0, kx0 + kxn).  Map 0: buf1 as
+// [(n0 + 1) rows1][n2] complex, box 16 x N/2.
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_constant__ Work<MAXI> W,
+                                                                  const __grid_constant__ TmaBatch<MAXI> maps)
 {
     using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
@@ -246,25 +253,29 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_c
     pdl_trigger();
     const TmaSmem s = tma_smem<N>(smem_raw, 1, NH);
     const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 16, units = a.kxn * zt;   // planes [kx0, kx0 + kxn)
+    const int nw = W.count();
     tma_bar_setup(s.bar);
-    const float2 *tw = C::twiddles(s.ex, a.tw1);
+    const float2 *tw = C::twiddles(s.ex, W.item[0].tw1);
     auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const int zt = b.n2 / 16;
         mbar_expect_tx(s.bar, NH * 128);
-        tma_load_2d(s.stage[0], &maps.m[0], (w % zt) * 16, (a.kx0 + w / zt) * a.rows1, s.bar);
+        tma_load_2d(s.stage[0], &maps.m[it_ub][0], (ub % zt) * 16, (b.kx0 + ub / zt) * b.rows1, s.bar);
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (tid == 0 && w < units) issue(w);
+    if (tid == 0 && w < nw) issue(w);
     const ColView sm{s.ex + col, 16};
-    for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
+    for (unsigned ph = 0; w < nw; w += gridDim.x, ph ^= 1) {
         const bool ok = mbar_wait(s.bar, ph);
-        const int kx = a.kx0 + w / zt, z = (w % zt) * 16 + col;
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / 16;
+        const int kx = a.kx0 + u / zt, z = (u % zt) * 16 + col;
         float2 v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? s.stage[0][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
         if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
-        if (tid == 0 && w + (int)gridDim.x < units) {
+        if (tid == 0 && w + (int)gridDim.x < nw) {
             fence_proxy_async();
             issue(w + gridDim.x);
         }
@@ -275,11 +286,11 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_c
 }
 
 // P4: buf0 (phi stream, 2 n1 rows) -> rows [0, n1) phi, rows [n1, 2 n1) -i k1 phi;
-// buf1 (E2 stream) -> rows [0, n1).  Unit: (k0, tile).  Maps 0 and 1: buf0 and
-// buf1 as [(n0 + 1) rows1][n2] complex, box 16 x min(N, 256).
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_constant__ PassArgs a,
-                                                                  const __grid_constant__ TmaMaps maps, int withE)
+// buf1 (E2 stream) -> rows [0, n1).  Unit: (k0, tile) over planes [kx0, kx0 + kxn).
+// Maps 0 and 1: buf0 and buf1 as [(n0 + 1) rows1][n2] complex, box 16 x min(N, 256).
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_constant__ Work<MAXI> W,
+                                                                  const __grid_constant__ TmaBatch<MAXI> maps, int withE)
 {
     using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T;
@@ -289,26 +300,29 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_c
     pdl_trigger();
     const TmaSmem s = tma_smem<N>(smem_raw, 2, N);
     const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    const int zt = a.n2 / 16, units = a.kxn * zt;   // planes [kx0, kx0 + kxn)
+    const int nw = W.count();
     tma_bar_setup(s.bar);
-    const float2 *tw = C::twiddles(s.ex, a.tw1);
+    const float2 *tw = C::twiddles(s.ex, W.item[0].tw1);
     auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const int zt = b.n2 / 16;
         mbar_expect_tx(s.bar, (withE ? 2 : 1) * N * 128);
-        const int x = (w % zt) * 16, y = (a.kx0 + w / zt) * a.rows1;
+        const int x = (ub % zt) * 16, y = (b.kx0 + ub / zt) * b.rows1;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            tma_load_2d(s.stage[0] + b * BOXR * 16, &maps.m[0], x, y + b * BOXR, s.bar);
-            if (withE) tma_load_2d(s.stage[1] + b * BOXR * 16, &maps.m[1], x, y + b * BOXR, s.bar);
+        for (int bx = 0; bx < NB; ++bx) {
+            tma_load_2d(s.stage[0] + bx * BOXR * 16, &maps.m[it_ub][0], x, y + bx * BOXR, s.bar);
+            if (withE) tma_load_2d(s.stage[1] + bx * BOXR * 16, &maps.m[it_ub][1], x, y + bx * BOXR, s.bar);
         }
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (tid == 0 && w < units) issue(w);
+    if (tid == 0 && w < nw) issue(w);
     const ColView sm{s.ex + col, 16};
-    const int n1 = a.n1;
-    for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
+    for (unsigned ph = 0; w < nw; w += gridDim.x, ph ^= 1) {
         const bool ok = mbar_wait(s.bar, ph);
-        const int kx = a.kx0 + w / zt, z = (w % zt) * 16 + col;
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / 16, n1 = a.n1;
+        const int kx = a.kx0 + u / zt, z = (u % zt) * 16 + col;
         float2 v[E], q[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -316,7 +330,7 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_c
             q[r] = withE ? s.stage[1][sw128(j + r * T, col)] : make_float2(0.f, 0.f);
         }
         if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
-        if (tid == 0 && w + (int)gridDim.x < units) {
+        if (tid == 0 && w + (int)gridDim.x < nw) {
             fence_proxy_async();
             issue(w + gridDim.x);
         }
@@ -343,10 +357,11 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_c
 // buf0 and buf1 as [n0 + 1][rows1][n2] complex, box 16 x 1 x N/2 (rows
 // k0 < n0); the Nyquist row k0 = n0 is read from global memory directly.
 // Stages: 0 the phi stream (buf0 row y), 1 the E1 stream (buf0 row n1 + y in
-// 3D, buf1 row y in 2D), 2 the E2 stream (buf1 row y, 3D).
-template <int N>
-__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p5_tma(const __grid_constant__ PassArgs a,
-                                                                  const __grid_constant__ TmaMaps maps)
+// 3D, buf1 row y in 2D), 2 the E2 stream (buf1 row y, 3D).  Which streams an
+// item has follows its outputs.
+template <int N, int MAXI>
+__global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p5_tma(const __grid_constant__ Work<MAXI> W,
+                                                                  const __grid_constant__ TmaBatch<MAXI> maps)
 {
     using C = TileCfg<N, 16>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
@@ -355,28 +370,33 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p5_tma(const __grid_c
     pdl_trigger();
     const TmaSmem s = tma_smem<N>(smem_raw, 3, NH);
     const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
-    float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
-    const bool first = phi || e0, second = e1 != nullptr, three = second && a.three_d;
-    const int zt = a.n2 / 16, units = a.n1 * zt;
+    const int nw = W.count();
     tma_bar_setup(s.bar);
-    const float2 *tw = C::twiddles(s.ex, a.tw0);
+    const float2 *tw = C::twiddles(s.ex, W.item[0].tw0);
     auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const bool first = b.out[0] || b.out[1], second = b.out[2] != nullptr, three = second && b.three_d;
+        const int zt = b.n2 / 16;
         mbar_expect_tx(s.bar, ((first ? 1 : 0) + (second ? 1 : 0) + (three ? 1 : 0)) * NH * 128);
-        const int x = (w % zt) * 16, y = w / zt;
-        if (first) tma_load_3d(s.stage[0], &maps.m[0], x, y, 0, s.bar);
+        const int x = (ub % zt) * 16, y = ub / zt;
+        if (first) tma_load_3d(s.stage[0], &maps.m[it_ub][0], x, y, 0, s.bar);
         if (second) {
-            if (a.three_d) tma_load_3d(s.stage[1], &maps.m[0], x, a.n1 + y, 0, s.bar);
-            else tma_load_3d(s.stage[1], &maps.m[1], x, y, 0, s.bar);
+            if (b.three_d) tma_load_3d(s.stage[1], &maps.m[it_ub][0], x, b.n1 + y, 0, s.bar);
+            else tma_load_3d(s.stage[1], &maps.m[it_ub][1], x, y, 0, s.bar);
         }
-        if (three) tma_load_3d(s.stage[2], &maps.m[1], x, y, 0, s.bar);
+        if (three) tma_load_3d(s.stage[2], &maps.m[it_ub][1], x, y, 0, s.bar);
     };
     pdl_wait();
     int w = blockIdx.x;
-    if (tid == 0 && w < units) issue(w);
+    if (tid == 0 && w < nw) issue(w);
     const ColView sm{s.ex + col, 16};
     constexpr int jN = NH % T, rN = NH / T;   // the thread and register holding k = NH
-    for (unsigned ph = 0; w < units; w += gridDim.x, ph ^= 1) {
-        const int y = w / zt, z = (w % zt) * 16 + col;
+    for (unsigned ph = 0; w < nw; w += gridDim.x, ph ^= 1) {
+        FSP_UNIT(W, w, a, u);
+        float *phi = a.out[0], *e0 = a.out[1], *e1 = a.out[2], *e2 = a.out[3];
+        const bool first = phi || e0, second = e1 != nullptr, three = second && a.three_d;
+        const int zt = a.n2 / 16;
+        const int y = u / zt, z = (u % zt) * 16 + col;
         // the Nyquist row (k0 = n0) of each stream, read directly
         float2 pN = make_float2(0.f, 0.f), YN = pN, ZN = pN;
         if (j == jN) {
@@ -406,7 +426,7 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p5_tma(const __grid_c
             q[r] = make_float2(Y.x - Z.y, Y.y + Z.x);        // Y + i Z
         }
         if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
-        if (tid == 0 && w + (int)gridDim.x < units) {
+        if (tid == 0 && w + (int)gridDim.x < nw) {
             fence_proxy_async();
             issue(w + gridDim.x);
         }
