@@ -89,7 +89,7 @@ void load_cache(const char *path, const std::string &arch)
             int N = std::atoi(key.c_str() + slash + 1);
             int li = length_index(N);
             for (int k = 0; k < PASS_KINDS && li >= 0; ++k)
-                if (name == kKindName[k] && val >= 0 && val < 8) g_var[k][li] = val;
+                if (name == kKindName[k] && val >= 0 && val < 16) g_var[k][li] = val;
         }
         pos = colon + 1;
     }
