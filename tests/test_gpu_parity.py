@@ -164,7 +164,7 @@ def test_solve_parity_more_lengths(fsp, oracle_mod, name, shape, h, method):
 
 @pytest.mark.parametrize("name,shape,h,method", LONG)
 def test_solve_parity_long_lines(fsp, oracle_mod, name, shape, h, method):
-    """The block-synchronous passes for 1024- to 8192-point lines against the oracle."""
+    """The long-line passes (multi-warp and block-synchronous) for 1024- to 8192-point lines against the oracle."""
     prob = _mixture(shape, h, seed=len(name))
     plan, rho32, phi, E = gpu_solve(fsp, prob, method)
     g = oracle_mod.kernel(method, list(shape), h)
@@ -368,6 +368,34 @@ def test_host_pipeline_matches_solve(fsp):
     for r, ph, E in zip(hosts, phis, Es):
         ph1, E1 = plan.solve(r.cuda())
         assert torch.equal(ph, ph1.cpu()) and torch.equal(E, E1.cpu())
+
+
+@pytest.mark.parametrize("shape,h,dtype,depth,with_phi,with_E", [
+    ((128, 96), (0.01, 0.02), "f32", 3, True, False),        # 2D, phi only, three slots
+    ((13, 17, 11), (0.05, 0.04, 0.06), "f64", 1, False, True),  # FP64 direct-sum plan, E only, one slot
+])
+def test_host_pipeline_modes(fsp, shape, h, dtype, depth, with_phi, with_E):
+    """The host pipe in other modes: 2D, FP64 plans, one or three slots, phi or E alone, pageable and pinned
+    host buffers; each result equals the plain solve's."""
+    np_dt, t_dt = (np.float32, torch.float32) if dtype == "f32" else (np.float64, torch.float64)
+    plan = fsp.Plan(shape, h, "vgf", dtype=dtype)
+    d = len(shape)
+    hosts = [torch.from_numpy(_mixture(shape, h, 90 + i).rho(np_dt)) for i in range(4)]
+    hosts = [x.pin_memory() if i % 2 else x for i, x in enumerate(hosts)]   # pinned and pageable
+    phis = [torch.empty(shape, dtype=t_dt) for _ in hosts] if with_phi else None
+    Es = [torch.empty((d,) + shape, dtype=t_dt) for _ in hosts] if with_E else None
+    pipe = fsp.HostPipeline(plan, depth=depth, with_phi=with_phi, with_E=with_E)
+    pipe.run(hosts, phis, Es)
+    torch.cuda.synchronize()
+    for i, r in enumerate(hosts):
+        ph1, E1 = plan.solve(r.cuda(), with_phi=with_phi, with_E=with_E)
+        if with_phi:
+            assert torch.equal(phis[i], ph1.cpu())
+        if with_E:
+            assert torch.equal(Es[i], E1.cpu())
+    pipe.close()
+    with pytest.raises(ValueError):
+        fsp.HostPipeline(plan, depth=2).run(hosts, None, None)   # outputs missing
 
 
 # --------------------------------------------------------------- autotuner
