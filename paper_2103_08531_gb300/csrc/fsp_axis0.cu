@@ -65,7 +65,7 @@ static int prep_one()
     using C = ColCfg<N>;
     int e = cudaFuncSetAttribute(p1_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if constexpr (N <= 512) {
-        e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
+        if constexpr (MAXI == 1) e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
         int b = 0;
         e |= cudaFuncSetAttribute(p1_adj_t<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1a<N>());
         e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p1_adj_t<N, MAXI>, TileCfg<N>::THREADS, smem_p1a<N>());
@@ -229,7 +229,12 @@ static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
         return chunked(items, n, kind == PASS_P1F ? units_p1f<N> : units_p5f<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
             if constexpr (N <= 512) {
-                return (var & 1) ? tile_launch<N, 8>(kind, w, var, st) : tile_launch<N, 16>(kind, w, var, st);
+                // the cp.async tiles serve single solves only (tuning variant bit 4);
+                // batches take the TMA tiles above
+                if constexpr (MAXI == 1)
+                    return (var & 1) ? tile_launch<N, 8>(kind, w, var, st) : tile_launch<N, 16>(kind, w, var, st);
+                else
+                    return (int)cudaErrorInvalidValue;
             } else {
                 const int total = w.offs[w.nitems];
                 if constexpr (!ColCfg<N>::WIDE) {

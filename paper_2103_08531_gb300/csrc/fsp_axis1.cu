@@ -58,7 +58,7 @@ static int prep_one()
     using C = ColCfg<N>;
     int e = cudaFuncSetAttribute(p2_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if constexpr (N <= 512) {
-        e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
+        if constexpr (MAXI == 1) e |= prep_tiles<N, MAXI, 16>() | prep_tiles<N, MAXI, 8>();
         int b = 0;
         e |= cudaFuncSetAttribute(p2_adj_t<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2a<N>());
         e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p2_adj_t<N, MAXI>, TileCfg<N>::THREADS, smem_p2a<N>());
@@ -192,7 +192,12 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
         return chunked(items, n, units_tile<N>, [&](auto &w) {
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
             if constexpr (N <= 512) {
-                return (var & 1) ? tile_launch<N, 8>(kind, w, flag, var, st) : tile_launch<N, 16>(kind, w, flag, var, st);
+                // the cp.async tiles serve single solves only (tuning variant bit 4);
+                // batches take the TMA tiles above
+                if constexpr (MAXI == 1)
+                    return (var & 1) ? tile_launch<N, 8>(kind, w, flag, var, st) : tile_launch<N, 16>(kind, w, flag, var, st);
+                else
+                    return (int)cudaErrorInvalidValue;
             } else {
                 const int total = w.offs[w.nitems];
                 if (kind == PASS_P2F) p2_fwd_blk<N, MAXI><<<total, ColCfg<N>::THREADS, ColCfg<N>::SMEM, st>>>(w);

@@ -1486,6 +1486,9 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     const int li = lane / T, j = lane % T;
     const int lines = a.kxn * a.rows1;       // lines of planes [kx0, kx0 + kxn)
     const int line0 = a.kx0 * a.rows1;
+    // line -> (k0, row): shifts when rows1 (2 n1, or 1 in 2D) is a power of two
+    const bool pow2 = (a.rows1 & (a.rows1 - 1)) == 0;
+    const int rsh = __ffs(a.rows1) - 1;
     const int groups = (lines + LPW - 1) / LPW;
     const int gstride = gridDim.x * C::WARPS;
     RowView<C::PAD> sm{smem + (warp * LPW + li) * C::RL};
@@ -1512,7 +1515,8 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
 #pragma unroll
         for (int r = 0; r < E; ++r) v[r] = r < E / 2 ? pv[r] : make_float2(0.f, 0.f);
         fetch(g + gstride);
-        const int kx = lc / a.rows1, row = lc % a.rows1;
+        const int kx = pow2 ? lc >> rsh : lc / a.rows1;
+        const int row = pow2 ? lc & (a.rows1 - 1) : lc % a.rows1;
         line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
         const float *Kr = krow(a, kx, row);
         float2 u[E];
