@@ -427,6 +427,14 @@ __device__ __forceinline__ void pair_exchange(float2 (&v)[E], const float2 *u, i
     }
 }
 
+// Does the pass with (NS, radices RAD) take the block-synchronous half exchange?
+template <int N, int E, int NS, int SYNC, class RAD>
+struct IsHalfPass : std::false_type {};
+template <int N, int E, int NS, int SYNC, int R, int... RS>
+struct IsHalfPass<N, E, NS, SYNC, Radices<R, RS...>>
+    : std::integral_constant<bool, FSP_HALF_XCH && SYNC == SYNC_BLOCK && N / E == 32 && E == R && 2 * NS * R == N &&
+                                       IsClosingRadix2<RS...>::value> {};
+
 template <int N, int E, bool INV, int NS, int R, int... RS, int SYNC, int TW, int OFF>
 struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
     template <bool PRUNE, class View>
@@ -440,8 +448,11 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
         // Block-synchronous form of the same lane-pair swap: only the half of
         // the outputs that changes thread goes through shared memory.  The
         // branches are warp-uniform in column tiles (j = tid / columns).
-        constexpr bool HALF = FSP_HALF_XCH && SYNC == SYNC_BLOCK && T == 32 && Q == 1 && 2 * NS * R == N &&
-                              IsClosingRadix2<RS...>::value;
+        // Its stores go to positions the storing thread itself read in the
+        // previous exchange (p = j mod 32), so that exchange needs no closing
+        // barrier before them.
+        constexpr bool HALF = IsHalfPass<N, E, NS, SYNC, Radices<R, RS...>>::value;
+        constexpr bool NEXT_HALF = IsHalfPass<N, E, NS * R, SYNC, Radices<RS...>>::value;
         static_assert(E % R == 0, "E must be a multiple of every radix");
         if constexpr (HALF) {
             const int k = j % NS;
@@ -451,26 +462,28 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
             pass_twiddles<N, R, INV, NS, TW, OFF>(u, tw, k);
             dft<R, INV>(u);
             const bool hi = (j & 16) != 0;
-            // output u of thread j sits at position hi N/2 + (j mod 16) + 16 u
+            // output u of thread j sits at position hi N/2 + (j mod 16) + 16 u;
+            // thread j parks what its partner j ^ 16 needs at j + 32 i (hi) or
+            // j + N/2 + 32 i (lo), slots that only thread j read before
             if (hi) {
 #pragma unroll
-                for (int i = 0; i < E / 2; ++i) sm.at(N / 2 + (j & 15) + 32 * i) = u[2 * i];
+                for (int i = 0; i < E / 2; ++i) sm.at(j + 32 * i) = u[2 * i];
             } else {
 #pragma unroll
-                for (int i = 0; i < E / 2; ++i) sm.at(j + 16 + 32 * i) = u[2 * i + 1];
+                for (int i = 0; i < E / 2; ++i) sm.at(j + N / 2 + 32 * i) = u[2 * i + 1];
             }
             lsync<SYNC>();
             if (hi) {
 #pragma unroll
                 for (int i = 0; i < E / 2; ++i) {
-                    v[i] = sm.at(j + 32 * i);
+                    v[i] = sm.at((j & 15) + N / 2 + 32 * i);
                     v[E / 2 + i] = u[2 * i + 1];
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < E / 2; ++i) {
                     v[i] = u[2 * i];
-                    v[E / 2 + i] = sm.at(j + 32 * (E / 2 + i));
+                    v[E / 2 + i] = sm.at(j + 16 + 32 * i);
                 }
             }
             lsync<SYNC>();
@@ -513,7 +526,7 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
             lsync<SYNC>();
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = sm.at(j + r * T);
-            lsync<SYNC>();
+            if constexpr (!NEXT_HALF) lsync<SYNC>();
             Passes<N, E, INV, NS * R, Radices<RS...>, SYNC, TW, NextOffT<TW, NS, R, OFF>::value>::template run<false>(v, j, tw,
                                                                                                          sm);
         }
