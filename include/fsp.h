@@ -191,7 +191,10 @@ int fsp_plan_set_pass_events(fsp_plan *plan, void *const *events, int count);
 int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, void *cuda_stream);
 
 /*
- * Autotuner.  Each pass has launch variants (bit 1: 8 instead of 16 values per
+ * Autotuner.  Each pass has launch variants (bit 4: the cp.async column tiles
+ * instead of the TMA-staged ones, and for middle passes of 1024-, 2048- and
+ * 8192-point lines the block-synchronous line kernel instead of the
+ * multi-warp or four-step one; bit 1, with bit 4: 8 instead of 16 values per
  * thread in column tiles; bit 2: one CTA per SM in persistent launches); the
  * choice is a process-wide table keyed by pass and padded length, read by
  * every solve.  fsp_autotune fills it for the passes this plan uses:

@@ -1,6 +1,7 @@
 // fsp_axis2.cu -- launchers of the axis-2 middle pass (P3: forward, kernel multiply, inverse).
 #include "fsp_internal.h"
 #include "fsp_launch.cuh"
+#include "fsp_long.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -60,6 +61,8 @@ static int prep_one()
         e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, p3_fwd_blk<N, MAXI>, C::THREADS, C::SMEM_STAGED);
         Occ2<N, MAXI>::p3 = std::max(1, b);
         e |= cudaFuncSetAttribute(p3_adj_blk<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if constexpr (N == L4S::N)
+            e |= cudaFuncSetAttribute(p3_fwd_4s<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L4S::P3_SMEM);
         if constexpr (kWide<N>) {
             using W = WideCfg<N>;
             int bw = 0;
@@ -136,6 +139,12 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
                                   C::SMEM, st, w, flag);
         } else {
             using C = RowCfg<N>;
+            // 8192-point lines: the four-step pass unless variant bit 4 asks for the block kernel
+            if constexpr (N == L4S::N) {
+                if (kind == PASS_P3F && !(var & 4))
+                    return launch_pdl_if(kLongPdl<N>, p3_fwd_4s<MAXI>, std::min(total, cap_sm), L4S::THREADS,
+                                         L4S::P3_SMEM, st, w, flag);
+            }
             if (kind == PASS_P3F)
                 return launch_pdl_if(kLongPdl<N>, p3_fwd_blk<N, MAXI>, std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::p3)),
                                   C::THREADS, C::SMEM_STAGED, st, w, flag);

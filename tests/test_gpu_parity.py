@@ -297,6 +297,23 @@ def test_batched_equals_single(fsp):
         assert torch.equal(bph, ph1) and torch.equal(bE, E1)
 
 
+def test_batched_2d_long_lines_equal_single(fsp, oracle_mod):
+    """2D items with 8192-point middle lines (the four-step 16 x 512 pass) in one batch: the
+    batched launch gives the single solves' bits, and those match the oracle."""
+    shapes = [((32, 4096), (0.02, 0.0005)), ((16, 4096), (0.03, 0.0004)), ((64, 4096), (0.01, 0.0005))]
+    plans = [fsp.Plan(s, h, "vgf") for s, h in shapes]
+    rhos32 = [_mixture(s, h, 70 + i).rho(np.float32) for i, (s, h) in enumerate(shapes)]
+    rhos = [torch.from_numpy(r).cuda() for r in rhos32]
+    phis, Es = fsp.solve_batched(plans, rhos)
+    for (s, h), p, r, r32, ph, E in zip(shapes, plans, rhos, rhos32, phis, Es):
+        ph1, E1 = p.solve(r)
+        assert torch.equal(ph, ph1) and torch.equal(E, E1)
+    s, h = shapes[0]
+    g = oracle_mod.kernel_vgf(list(s), h)
+    p_ref, E_ref = oracle_mod.solve_with_kernel(g, rhos32[0].astype(np.float64), h)
+    assert rel(phis[0].cpu(), p_ref) <= TOL and rel(Es[0].cpu(), E_ref) <= TOL
+
+
 def test_batched_many_mixed_items_and_graph(fsp):
     """More items than one launch holds (chunks), 2D and 3D mixed, uneven shapes; graph replay."""
     rng = np.random.default_rng(44)
@@ -413,7 +430,8 @@ def _write_cache(path, arch, shape, var_tile, var_p3):
 
 @pytest.mark.parametrize("shape,h", [((64, 64, 32), (0.02, 0.025, 0.03)), ((32, 128, 64), (0.03, 0.01, 0.02)),
                                      ((128, 64), (0.01, 0.02)), ((32, 64, 128), (0.03, 0.02, 0.01)),
-                                     ((32, 32, 256), (0.03, 0.02, 0.005)), ((32, 32, 512), (0.03, 0.02, 0.004))])
+                                     ((32, 32, 256), (0.03, 0.02, 0.005)), ((32, 32, 512), (0.03, 0.02, 0.004)),
+                                     ((32, 4096), (0.02, 0.0005))])
 def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     """Each launch variant the autotuner can pick gives the oracle's answer."""
     cap = torch.cuda.get_device_capability()
@@ -428,7 +446,8 @@ def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     try:
         # column tiles: 0 TMA-staged group tiles, 2 the same one CTA per SM, 4 / 5 the cp.async
         # block tiles with 16 / 8 values per thread, 6 / 7 those one CTA per SM
-        # middle pass (bits 2 and, at 2n = 1024 / 2048, 4): the same bits of vt
+        # middle pass (bits 2 and, at 2n = 1024 / 2048, 4): the same bits of vt; at 2n = 8192
+        # bit 4 takes the block-synchronous line kernel instead of the four-step pass
         for vt, vp in [(0, 0), (2, 2), (4, 4), (5, 4), (6, 6), (7, 6)]:
             _write_cache(path, arch, shape, vt, vp)
             plan.autotune(path, 0)
