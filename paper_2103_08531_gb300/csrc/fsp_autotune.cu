@@ -6,7 +6,9 @@
 // (not 192); 2 = one CTA per SM in the persistent launches instead of as many
 // as fit.  For the middle pass at 2n = 1024 and 2048, bit 4 selects the
 // block-synchronous line kernel instead of the multi-warp-per-line one, and at
-// 2n = 8192 instead of the four-step (16 x 512) pass.  The table is process-wide,
+// 2n = 8192 instead of the four-step (16 x 512) pass; for P5 at 2n = 8192 it
+// selects the staged block-synchronous columns instead of the four-step
+// through global memory.  The table is process-wide,
 // keyed by pass kind and padded length, and is read by every solve.  A small
 // JSON file caches it per GPU architecture, e.g.
 //   {"sm_103": {"p3_fwd/512": 0, "p4_fwd/512": 2}}
@@ -47,7 +49,7 @@ std::vector<int> candidates(int kind, int N)
     const bool tile = kind == PASS_P1F || kind == PASS_P2F || kind == PASS_P4F || kind == PASS_P5F;
     if (N > 512) {
         if (kind == PASS_P3F && (N == 768 || N == 1024 || N == 2048)) return {0, 2, 4, 6};
-        if (kind == PASS_P3F && N == 8192) return {0, 4};
+        if ((kind == PASS_P3F || kind == PASS_P5F) && N == 8192) return {0, 4};
         return {0};
     }
     if (tile) return N == 192 ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0, 2, 4, 5, 6, 7};

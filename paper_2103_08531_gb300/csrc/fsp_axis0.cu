@@ -1,6 +1,7 @@
 // fsp_axis0.cu -- launchers of the axis-0 passes (P1 real -> half spectrum, P5 back).
 #include "fsp_internal.h"
 #include "fsp_launch.cuh"
+#include "fsp_long.cuh"
 #include "fsp_tma.cuh"
 
 #include <algorithm>
@@ -107,11 +108,78 @@ static int prep_tma()
     return e;
 }
 
+static constexpr size_t smem_p5_4s_b() { return TmaTile<512>::smem(1, 512); }
+
 template <int N>
 static int prep()
 {
     int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
     if constexpr (N <= 512) e |= prep_tma<N, 1>() | prep_tma<N, BATCH_MAX>();
+    if constexpr (N == L4S::N) {
+        e |= cudaFuncSetAttribute(p5_4s_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_4s_b());
+        e |= cudaFuncSetAttribute(p5_4s_b<BATCH_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_4s_b());
+    }
+    return e;
+}
+
+// P5 of 2D solves with 2 n0 = 8192: the four-step through global memory
+// (p5_4s_a / p5_4s_b in fsp_long.cuh), in place in buf0 and buf1.  Every item
+// 2D with whole 16-column tiles.
+static bool fits_p5_4s(const PassArgs *items, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (items[i].three_d || items[i].n2 % 16) return false;
+    return true;
+}
+static bool wants_e1(const PassArgs &a) { return a.out[2] != nullptr; }
+static bool wants_01(const PassArgs &a) { return a.out[0] != nullptr || a.out[1] != nullptr; }
+static int blocks_a(const PassArgs &a) { return (257 * (a.n2 / 2) + 255) / 256; }
+static int units_a0(const PassArgs &a) { return wants_e1(a) ? blocks_a(a) : 0; }
+static int units_a1(const PassArgs &a) { return wants_01(a) ? blocks_a(a) : 0; }
+static int units_b0(const PassArgs &a) { return wants_e1(a) ? 8 * (a.n2 / 16) : 0; }
+static int units_b1(const PassArgs &a) { return wants_01(a) ? 2 * 8 * (a.n2 / 16) : 0; }
+
+template <class Wk>
+static int launch_p5_4s_b(const Wk &w, int mode, cudaStream_t st)
+{
+    constexpr int MAXI = Wk::max_items;
+    TmaBatch<MAXI> m;
+    std::memset(&m, 0, sizeof(m));
+    for (int i = 0; i < w.nitems; ++i) {
+        const PassArgs &a = w.item[i];
+        const unsigned long long dims[2] = {(unsigned long long)a.n2, (unsigned long long)a.n0 + 1};
+        const unsigned long long str[1] = {(unsigned long long)a.n2 * 8};
+        const unsigned box[2] = {16, 256};
+        if ((a.buf0 && encode_tensor_map(&m.m[i][0], a.buf0, 2, 8, dims, str, box)) ||
+            (a.buf1 && encode_tensor_map(&m.m[i][1], a.buf1, 2, 8, dims, str, box)))
+            return (int)cudaErrorInvalidValue;
+    }
+    const int total = w.offs[w.nitems];
+    return launch_pdl(p5_4s_b<MAXI>, std::min(total, sm_count()), TileCfg<512, 16>::THREADS, smem_p5_4s_b(), st, w,
+                      m, mode);
+}
+
+static int run_p5_4s(const PassArgs *items, int n, cudaStream_t st)
+{
+    auto step_a = [&](int mode) {
+        return chunked(items, n, mode ? units_a1 : units_a0, [&](auto &w) {
+            constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+            const int total = w.offs[w.nitems];
+            if (total == 0) return 0;
+            return launch_pdl(p5_4s_a<MAXI>, std::min(total, 8 * sm_count()), 256, 0, st, w, mode);
+        });
+    };
+    auto step_b = [&](int mode) {
+        return chunked(items, n, mode ? units_b1 : units_b0, [&](auto &w) {
+            if (w.offs[w.nitems] == 0) return 0;
+            return launch_p5_4s_b(w, mode, st);
+        });
+    };
+    // E1 first: its set lives in buf1, which the E0 set overwrites afterwards
+    int e = step_a(0);
+    if (!e) e = step_b(0);
+    if (!e) e = step_a(1);
+    if (!e) e = step_b(1);
     return e;
 }
 
@@ -224,6 +292,9 @@ static int run(int kind, const PassArgs *items, int n, int var, cudaStream_t st)
                 return chunked(items, n, kind == PASS_P1F ? units_p1_tma<N> : units_p5_tma<N>,
                                [&](auto &w) { return tma_launch0<N>(kind, w, var, st); });
         }
+    }
+    if constexpr (N == L4S::N) {   // variant bit 4: the staged block-synchronous columns instead
+        if (kind == PASS_P5F && !(var & 4) && fits_p5_4s(items, n)) return run_p5_4s(items, n, st);
     }
     if (kind == PASS_P1F || kind == PASS_P5F) {
         return chunked(items, n, kind == PASS_P1F ? units_p1f<N> : units_p5f<N>, [&](auto &w) {

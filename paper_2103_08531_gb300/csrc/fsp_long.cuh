@@ -214,4 +214,167 @@ __global__ void __launch_bounds__(L4S::THREADS, 1) p3_fwd_4s(const __grid_consta
     }
 }
 
+// ------------------------------------------------ C2R columns through HBM
+//
+// The first-axis inverse of 2D solves with 2 n0 = 8192 as a four-step split
+// through global memory, k = 512 k1 + k2 and n = n1 + 16 n2:
+//   x[n1 + 16 n2] = sum_k2 W_512^(-n2 k2) W_8192^(-n1 k2) sum_k1 X[512 k1 + k2] W_16^(-n1 k1).
+// Two columns z0 = 2p, z0 + 1 with half spectra A, B (rows k0 <= NH of a
+// buffer) are packed as A + i B, each extended by conjugate symmetry; the
+// inverse of the pack is a(z0) + i b(z0 + 1).
+// Step 1 (p5_4s_a): the 16-point inverses over k1 with the twiddles
+// W_8192^(-n1 k2).  For k2 = t and k2 = 512 - t the inputs are the same 16
+// rows (512 a + t, a < 8, and their mirrors 512 b - t, b = 1 .. 8), so one
+// thread takes both and writes Y[n1][k2] back into those rows: Y[n1][k2] of
+// the pair goes to row 512 (n1 mod 8) + k2, column z0 + (n1 >= 8).  Every
+// (row, pair) slot is read and written by one thread only; row NH is read
+// (t = 0) and not written.
+// Step 2 (p5_4s_b): for fixed n1 = 8 h + a the 512 values Y[n1][k2] are rows
+// 512 a .. 512 a + 511 of column 2p + h: a tile pass of 512-point inverses
+// over 16 columns, first half kept (n2 < 256), Re -> the field at z0, Im ->
+// at z0 + 1.
+// Sets: mode 0 takes buf1 (the E1 stream) in place; mode 1 takes buf0 and
+// writes the phi set in place (when phi is wanted) and the -i k0 (A + i B)
+// set, E0, into buf1 at the same places.  Mode 0 and its step 2 therefore run
+// before mode 1.  No workspace beyond buf0 and buf1.
+
+// Step 1.  Unit: a block of 256 threads over (t in [0, 256], pair), pairs
+// fastest; mode 0 or 1 for the whole launch.
+template <int MAXI>
+__global__ void __launch_bounds__(256) p5_4s_a(const __grid_constant__ Work<MAXI> W, int mode)
+{
+    constexpr int N = L4S::N, NH = L4S::NH;
+    pdl_trigger();
+    pdl_wait();
+    const int nw = W.count();
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        FSP_UNIT(W, w, a, u);
+        const int pairs = a.n2 / 2;
+        const int idx = u * 256 + (int)threadIdx.x;
+        if (idx >= 257 * pairs) continue;
+        const int t = idx / pairs, p = idx % pairs;
+        float2 *buf = mode ? a.buf0 : a.buf1;
+        const bool want0 = mode ? a.out[0] != nullptr : true;   // the set written in place
+        const bool want1 = mode && a.out[1] != nullptr;          // -i k0 set into buf1
+        const float4 *col = reinterpret_cast<const float4 *>(buf + 2 * p);
+        const size_t ld = (size_t)a.n2 / 2;   // row stride in float4
+        float4 R[8], M[8];   // rows 512 a + t and 512 b - t (b = a + 1)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            R[i] = col[(size_t)(512 * i + t) * ld];
+            M[i] = col[(size_t)(512 * (i + 1) - t) * ld];
+        }
+        const float2 *tw = a.tw0;   // the 8192-point table
+        // one k2 = tt of the pair of offsets; sel 0: tt = t, 1: tt = 512 - t
+        auto one = [&](int tt, int sel, bool withk, float2 *dst) {
+            float2 x[16];
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const int k = 512 * k1 + tt;
+                float4 q;
+                bool cj;
+                if (sel == 0) {   // k1 < 8: row 512 k1 + t; else the mirror row 512 (16 - k1) - t
+                    q = k1 < 8 ? R[k1] : M[15 - k1];
+                    cj = k > NH;
+                } else {          // k1 < 8: row 512 (k1 + 1) - t; else the mirror row 512 (15 - k1) + t
+                    q = k1 < 8 ? M[k1] : R[15 - k1];
+                    cj = k1 >= 8;
+                }
+                if (cj) {
+                    q.y = -q.y;
+                    q.w = -q.w;
+                }
+                float2 v = make_float2(q.x - q.w, q.y + q.z);   // A + i B
+                if (withk) {
+                    const float kk = wave(k, NH, a.k0s);
+                    v = make_float2(kk * v.y, -kk * v.x);          // -i k0 (A + i B)
+                }
+                x[k1] = v;
+            }
+            dft<16, true>(x);
+            twiddle16<true>(x, tw_base(tw, tt));
+            float4 *o = reinterpret_cast<float4 *>(dst + 2 * p);
+#pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1)
+                o[(size_t)(512 * n1 + tt) * ld] = make_float4(x[n1].x, x[n1].y, x[n1 + 8].x, x[n1 + 8].y);
+        };
+        const bool two = t != 0 && t != 256;
+        // every load is done above, so the in-place stores cannot overwrite an input
+        if (want1) {
+            one(t, 0, true, a.buf1);
+            if (two) one(512 - t, 1, true, a.buf1);
+        }
+        if (want0) {
+            one(t, 0, false, buf);
+            if (two) one(512 - t, 1, false, buf);
+        }
+    }
+}
+
+// Step 2.  Unit: (set, a < 8, tile of 16 columns); mode 0: one set, buf1 ->
+// E1; mode 1: set 0 buf0 -> phi, set 1 buf1 -> E0 (a set nobody asked for is
+// skipped).  Maps 0 and 1: buf0 and buf1 as [n0 + 1][n2] complex, box 16 x
+// 256, 128-byte swizzle; the column tile engine of the 512-point passes.
+template <int MAXI>
+__global__ void __launch_bounds__(TileCfg<512, 16>::THREADS) p5_4s_b(const __grid_constant__ Work<MAXI> W,
+                                                                     const __grid_constant__ TmaBatch<MAXI> maps,
+                                                                     int mode)
+{
+    constexpr int N = 512;
+    using C = TileCfg<N, 16>;
+    constexpr int E = C::E, T = C::T;
+    using RAD = typename C::RAD;
+    extern __shared__ unsigned char smem_raw[];
+    pdl_trigger();
+    const TmaSmem s = tma_smem<N>(smem_raw, 1, N);
+    const int tid = threadIdx.x, col = tid % 16, j = tid / 16;
+    const int nw = W.count();
+    tma_bar_setup(s.bar);
+    // the 512-point table, W_512^m = W_8192^(16 m), where the tile engine keeps its copy
+    float2 *stw = s.ex + N * 16;
+    for (int i = tid; i < N; i += C::THREADS) stw[i] = __ldg(W.item[0].tw0 + 16 * i);
+    __syncthreads();
+    auto field = [&](const PassArgs &b, int set) -> float * { return mode == 0 ? b.out[2] : b.out[set]; };
+    auto next_active = [&](int w) -> int {
+        for (; w < nw; w += gridDim.x) {
+            FSP_UNIT(W, w, b, ub);
+            if (field(b, ub / (8 * (b.n2 / 16)))) break;
+        }
+        return w;
+    };
+    auto issue = [&](int w) {
+        FSP_UNIT(W, w, b, ub);
+        const int zt = b.n2 / 16, set = ub / (8 * zt), r = ub % (8 * zt);
+        const CUtensorMap *m = &maps.m[it_ub][(mode == 0 || set == 1) ? 1 : 0];
+        mbar_expect_tx(s.bar, N * 128);
+        tma_load_2d(s.stage[0], m, (r % zt) * 16, 512 * (r / zt), s.bar);
+        tma_load_2d(s.stage[0] + 256 * 16, m, (r % zt) * 16, 512 * (r / zt) + 256, s.bar);
+    };
+    pdl_wait();
+    int w = next_active(blockIdx.x);
+    if (tid == 0 && w < nw) issue(w);
+    const ColView sm{s.ex + col, 16};
+    for (unsigned ph = 0; w < nw; ph ^= 1) {
+        const bool ok = mbar_wait(s.bar, ph);
+        FSP_UNIT(W, w, a, u);
+        const int zt = a.n2 / 16, set = u / (8 * zt), r = u % (8 * zt);
+        const int n1 = 8 * (col & 1) + r / zt, pcol = ((r % zt) * 16 + col) >> 1;
+        float *out = field(a, set);
+        float2 v[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = s.stage[0][sw128(j + q * T, col)];
+        if (tma_tile_failed(ok, s.bar, ph, a.status)) break;
+        const int wn = next_active(w + gridDim.x);
+        if (tid == 0 && wn < nw) {
+            fence_proxy_async();
+            issue(wn);
+        }
+        tile_fft<N, E, true, false, RAD>(v, j, stw, sm);
+#pragma unroll
+        for (int q = 0; q < E / 2; ++q)
+            *reinterpret_cast<float2 *>(out + gidx(a, n1 + 16 * (j + q * T), 0, 2 * pcol)) = v[q];
+        w = wn;
+    }
+}
+
 } // namespace fsp

@@ -298,9 +298,11 @@ def test_batched_equals_single(fsp):
 
 
 def test_batched_2d_long_lines_equal_single(fsp, oracle_mod):
-    """2D items with 8192-point middle lines (the four-step 16 x 512 pass) in one batch: the
-    batched launch gives the single solves' bits, and those match the oracle."""
-    shapes = [((32, 4096), (0.02, 0.0005)), ((16, 4096), (0.03, 0.0004)), ((64, 4096), (0.01, 0.0005))]
+    """2D items with 8192-point lines in one batch (the four-step middle pass; the four-step C2R
+    columns through buf0 / buf1): the batched launches give the single solves' bits, and those
+    match the oracle."""
+    shapes = [((32, 4096), (0.02, 0.0005)), ((16, 4096), (0.03, 0.0004)), ((64, 4096), (0.01, 0.0005)),
+              ((4096, 32), (0.0005, 0.02)), ((4096, 64), (0.0004, 0.01))]
     plans = [fsp.Plan(s, h, "vgf") for s, h in shapes]
     rhos32 = [_mixture(s, h, 70 + i).rho(np.float32) for i, (s, h) in enumerate(shapes)]
     rhos = [torch.from_numpy(r).cuda() for r in rhos32]
@@ -312,6 +314,18 @@ def test_batched_2d_long_lines_equal_single(fsp, oracle_mod):
     g = oracle_mod.kernel_vgf(list(s), h)
     p_ref, E_ref = oracle_mod.solve_with_kernel(g, rhos32[0].astype(np.float64), h)
     assert rel(phis[0].cpu(), p_ref) <= TOL and rel(Es[0].cpu(), E_ref) <= TOL
+
+
+def test_2d_8192_columns_phi_only_and_E_only(fsp):
+    """The four-step C2R columns with only phi (no buf1) or only E (no phi set) requested."""
+    shape, h = (4096, 64), (0.0004, 0.01)
+    rho = torch.from_numpy(_mixture(shape, h, seed=81).rho(np.float32)).cuda()
+    plan = fsp.Plan(shape, h, "vgf")
+    phi, E = plan.solve(rho)
+    phi1, none = plan.solve(rho, with_E=False)
+    none2, E1 = plan.solve(rho, with_phi=False)
+    assert none is None and none2 is None
+    assert torch.equal(phi1, phi) and torch.equal(E1, E)
 
 
 def test_batched_many_mixed_items_and_graph(fsp):
@@ -431,7 +445,7 @@ def _write_cache(path, arch, shape, var_tile, var_p3):
 @pytest.mark.parametrize("shape,h", [((64, 64, 32), (0.02, 0.025, 0.03)), ((32, 128, 64), (0.03, 0.01, 0.02)),
                                      ((128, 64), (0.01, 0.02)), ((32, 64, 128), (0.03, 0.02, 0.01)),
                                      ((32, 32, 256), (0.03, 0.02, 0.005)), ((32, 32, 512), (0.03, 0.02, 0.004)),
-                                     ((32, 4096), (0.02, 0.0005))])
+                                     ((32, 4096), (0.02, 0.0005)), ((4096, 32), (0.0005, 0.02))])
 def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     """Each launch variant the autotuner can pick gives the oracle's answer."""
     cap = torch.cuda.get_device_capability()
@@ -447,7 +461,8 @@ def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
         # column tiles: 0 TMA-staged group tiles, 2 the same one CTA per SM, 4 / 5 the cp.async
         # block tiles with 16 / 8 values per thread, 6 / 7 those one CTA per SM
         # middle pass (bits 2 and, at 2n = 1024 / 2048, 4): the same bits of vt; at 2n = 8192
-        # bit 4 takes the block-synchronous line kernel instead of the four-step pass
+        # bit 4 takes the block-synchronous line kernel instead of the four-step pass, and for
+        # 8192-point columns (P5) the staged block kernel instead of the four-step through HBM
         for vt, vp in [(0, 0), (2, 2), (4, 4), (5, 4), (6, 6), (7, 6)]:
             _write_cache(path, arch, shape, vt, vp)
             plan.autotune(path, 0)
