@@ -1,5 +1,6 @@
 // fsp_long.cuh -- 8192-point lines of the 2D solve (2n = 8192, a 4096^2 grid)
-// as a four-step split inside one CTA: 8192 = 16 x 512.
+// as four-step splits, 8192 = 16 x 512: inside one CTA for the middle pass,
+// through global memory for the C2R columns.
 //
 // Forward (n = 512 n1 + n2, k = k1 + 16 k2):
 //   X[k1 + 16 k2] = sum_n2 W_512^(n2 k2) W_8192^(n2 k1) sum_n1 x[512 n1 + n2] W_16^(n1 k1)
@@ -14,10 +15,10 @@
 // Against one block-synchronous 8192-point transform (four radix passes,
 // three exchanges of the whole line through shared memory, two block barriers
 // each) a line needs two block barriers per transform, and the 512-point
-// parts run on 16 independent warps.  (The first-axis columns of these
-// solves keep their block-synchronous kernels: with only two columns on chip
-// per CTA they are bound by 8- and 16-byte row accesses, which this split
-// does not change.)
+// parts run on 16 independent warps.  The C2R columns (axis 0) cannot hold
+// more than two such columns per CTA, so they take the split through global
+// memory instead (p5_4s_a / p5_4s_b below), where every access is a whole
+// row segment of 16 or 32 columns.
 #pragma once
 
 #include "fsp_tma.cuh"
