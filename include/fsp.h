@@ -195,13 +195,17 @@ int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, void *cuda_s
  * instead of the TMA-staged ones, and for middle passes of 1024-, 2048- and
  * 8192-point lines the block-synchronous line kernel instead of the
  * multi-warp or four-step one; bit 1, with bit 4: 8 instead of 16 values per
- * thread in column tiles; bit 2: one CTA per SM in persistent launches); the
+ * thread in column tiles; bit 2: one CTA per SM in persistent launches; bit 8,
+ * without bit 4, at padded lengths 128, 256 and 512: a second radix split of
+ * the transforms, 8 x 16, 8 x 8 x 4 and 8 x 8 x 8 instead of 16 x 8, 16 x 16
+ * and 16 x 16 x 2, in the TMA column tiles and the single-solve middle pass); the
  * choice is a process-wide table keyed by pass and padded length, read by
  * every solve.  fsp_autotune fills it for the passes this plan uses:
  * mode 0 reads the JSON cache at cache_path (may be NULL) only; mode 1 reads
  * it and times the missing passes on this plan's geometry; mode 2 times all
  * of them.  With a cache_path the table is written back, keyed by GPU
- * architecture.  This call allocates scratch buffers and synchronises (it is
+ * architecture.  With FSP_TUNE_LOG set in the environment every timed variant
+ * is reported on stderr.  This call allocates scratch buffers and synchronises (it is
  * set-up, not a solve).  fsp_tuned_variant reports an entry: kind is 0..7 for
  * p1_fwd, p1_adj, p2_fwd, p2_adj, p3_fwd, p3_adj, p4_fwd, p5_fwd.  Direct-path
  * plans have nothing to tune (mode 0 behaviour).

@@ -4,7 +4,9 @@
 // the TMA-staged ones (lengths <= 512; single solves: batches keep the
 // defaults); 1 = with bit 4, 8 values per thread in those tiles instead of 16
 // (not 192); 2 = one CTA per SM in the persistent launches instead of as many
-// as fit.  For the middle pass at 2n = 1024 and 2048, bit 4 selects the
+// as fit; 8 = without bit 4, the second radix split of the length (Plan16B:
+// 8 x 16 at 128, 8 x 8 x 4 at 256, 8 x 8 x 8 at 512, instead of 16 x 8,
+// 16 x 16 and 16 x 16 x 2) in the TMA tiles and the single-solve middle pass.  For the middle pass at 2n = 1024 and 2048, bit 4 selects the
 // block-synchronous line kernel instead of the multi-warp-per-line one, and at
 // 2n = 8192 instead of the four-step (16 x 512) pass; for P5 at 2n = 8192 it
 // selects the staged block-synchronous columns instead of the four-step
@@ -16,6 +18,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -52,9 +55,13 @@ std::vector<int> candidates(int kind, int N)
         if ((kind == PASS_P3F || kind == PASS_P5F) && N == 8192) return {0, 4};
         return {0};
     }
-    if (tile) return N == 192 ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0, 2, 4, 5, 6, 7};
-    if (kind == PASS_P3F || kind == PASS_P3A) return {0, 2};
-    return {0};
+    std::vector<int> c;
+    if (tile) c = N == 192 ? std::vector<int>{0, 2, 4, 6} : std::vector<int>{0, 2, 4, 5, 6, 7};
+    else if (kind == PASS_P3F || kind == PASS_P3A) c = {0, 2};
+    else c = {0};
+    // the second radix split (the TMA tiles and the single-solve middle pass)
+    if ((tile || kind == PASS_P3F) && has_radix_plan_b(N)) c.insert(c.end(), {8, 10});
+    return c;
 }
 
 std::string arch_key()
@@ -204,6 +211,8 @@ static int autotune(fsp_plan *plan, const char *cache_path, int mode)
         std::sort(t.begin(), t.end());
         return t[t.size() / 2];
     };
+    // FSP_TUNE_LOG set: every timed variant is reported on stderr
+    const bool log = std::getenv("FSP_TUNE_LOG") != nullptr;
     for (const Job &j : jobs) {
         if (rc != FSP_OK) break;
         const int li = length_index(j.N);
@@ -218,6 +227,7 @@ static int autotune(fsp_plan *plan, const char *cache_path, int mode)
                 rc = FSP_ERR_CUDA;
                 break;
             }
+            if (log) std::fprintf(stderr, "fsp_autotune %s/%d variant %d: %.4f ms\n", kKindName[j.kind], j.N, v, ms);
             if (ms < best) {
                 best = ms;
                 best_v = v;

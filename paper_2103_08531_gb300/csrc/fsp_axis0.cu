@@ -84,7 +84,7 @@ static int prep_one()
 }
 
 // TMA-staged column tiles (2n <= 512), single solves (MAXI = 1) and batches
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 struct TmaOcc0 {
     static inline int p1 = 1, p5 = 1;
 };
@@ -94,17 +94,17 @@ template <int N>
 static constexpr size_t smem_p5_tma() { return TmaTile<N>::smem(3, N / 2); }
 static_assert(sizeof(Work<BATCH_MAX>) + sizeof(TmaBatch<BATCH_MAX>) + 16 <= 32764, "kernel parameters too large");
 
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 static int prep_tma()
 {
     int e = 0, b1 = 0, b5 = 0;
-    using C = TileCfg<N, 16>;
-    e |= cudaFuncSetAttribute(p1_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1_tma<N>());
-    e |= cudaFuncSetAttribute(p5_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_tma<N, MAXI>, C::THREADS, smem_p1_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_tma<N, MAXI>, C::THREADS, smem_p5_tma<N>());
-    TmaOcc0<N, MAXI>::p1 = std::max(1, b1);
-    TmaOcc0<N, MAXI>::p5 = std::max(1, b5);
+    using C = TileCfg<N, 16, ALT>;
+    e |= cudaFuncSetAttribute(p1_tma<N, MAXI, ALT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p1_tma<N>());
+    e |= cudaFuncSetAttribute(p5_tma<N, MAXI, ALT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p1_tma<N, MAXI, ALT>, C::THREADS, smem_p1_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, p5_tma<N, MAXI, ALT>, C::THREADS, smem_p5_tma<N>());
+    TmaOcc0<N, MAXI, ALT>::p1 = std::max(1, b1);
+    TmaOcc0<N, MAXI, ALT>::p5 = std::max(1, b5);
     return e;
 }
 
@@ -115,6 +115,7 @@ static int prep()
 {
     int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
     if constexpr (N <= 512) e |= prep_tma<N, 1>() | prep_tma<N, BATCH_MAX>();
+    if constexpr (N <= 512 && Plan16B<N>::HAS) e |= prep_tma<N, 1, 1>();
     if constexpr (N == L4S::N) {
         e |= cudaFuncSetAttribute(p5_4s_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_4s_b());
         e |= cudaFuncSetAttribute(p5_4s_b<BATCH_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_4s_b());
@@ -189,7 +190,8 @@ template <int N>
 static int units_p5_tma(const PassArgs &a) { return a.n1 * (a.n2 / 16); }
 
 // The TMA-staged P1 / P5 of one launch's items: tensor maps of every item
-// built here from its own buffers.
+// built here from its own buffers.  Variant bits: 2 = one CTA per SM; 8 = the
+// second radix split (single solves, lengths that have one).
 template <int N, class Wk>
 static int tma_launch0(int kind, const Wk &w, int var, cudaStream_t st)
 {
@@ -217,11 +219,18 @@ static int tma_launch0(int kind, const Wk &w, int var, cudaStream_t st)
     }
     const int total = w.offs[w.nitems];
     const int sms = sm_count();
-    if (kind == PASS_P1F)
-        return launch_pdl(p1_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc0<N, MAXI>::p1)), C::THREADS,
-                          smem_p1_tma<N>(), st, w, m);
-    return launch_pdl(p5_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc0<N, MAXI>::p5)), C::THREADS,
-                      smem_p5_tma<N>(), st, w, m);
+    auto go = [&](auto alt) {
+        constexpr int ALT = decltype(alt)::value;
+        using O = TmaOcc0<N, MAXI, ALT>;
+        if (kind == PASS_P1F)
+            return launch_pdl(p1_tma<N, MAXI, ALT>, std::min(total, sms * ((var & 2) ? 1 : O::p1)), C::THREADS,
+                              smem_p1_tma<N>(), st, w, m);
+        return launch_pdl(p5_tma<N, MAXI, ALT>, std::min(total, sms * ((var & 2) ? 1 : O::p5)), C::THREADS,
+                          smem_p5_tma<N>(), st, w, m);
+    };
+    if constexpr (MAXI == 1 && Plan16B<N>::HAS)
+        if (var & 8) return go(std::integral_constant<int, 1>{});
+    return go(std::integral_constant<int, 0>{});
 }
 
 int prepare_axis0(int N)

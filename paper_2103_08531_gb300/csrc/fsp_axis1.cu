@@ -71,7 +71,7 @@ static int prep_one()
 }
 
 // TMA-staged column tiles (2n <= 512), single solves (MAXI = 1) and batches
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 struct TmaOcc1 {
     static inline int p2 = 1, p4 = 1;
 };
@@ -80,17 +80,17 @@ static constexpr size_t smem_p2_tma() { return TmaTile<N>::smem(1, N / 2); }
 template <int N>
 static constexpr size_t smem_p4_tma() { return TmaTile<N>::smem(2, N); }
 
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 static int prep_tma()
 {
     int e = 0, b2 = 0, b4 = 0;
-    using C = TileCfg<N, 16>;
-    e |= cudaFuncSetAttribute(p2_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2_tma<N>());
-    e |= cudaFuncSetAttribute(p4_tma<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_tma<N, MAXI>, C::THREADS, smem_p2_tma<N>());
-    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_tma<N, MAXI>, C::THREADS, smem_p4_tma<N>());
-    TmaOcc1<N, MAXI>::p2 = std::max(1, b2);
-    TmaOcc1<N, MAXI>::p4 = std::max(1, b4);
+    using C = TileCfg<N, 16, ALT>;
+    e |= cudaFuncSetAttribute(p2_tma<N, MAXI, ALT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2_tma<N>());
+    e |= cudaFuncSetAttribute(p4_tma<N, MAXI, ALT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p4_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, p2_tma<N, MAXI, ALT>, C::THREADS, smem_p2_tma<N>());
+    e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, p4_tma<N, MAXI, ALT>, C::THREADS, smem_p4_tma<N>());
+    TmaOcc1<N, MAXI, ALT>::p2 = std::max(1, b2);
+    TmaOcc1<N, MAXI, ALT>::p4 = std::max(1, b4);
     return e;
 }
 
@@ -99,6 +99,7 @@ static int prep()
 {
     int e = prep_one<N, 1>() | prep_one<N, BATCH_MAX>();
     if constexpr (N <= 512) e |= prep_tma<N, 1>() | prep_tma<N, BATCH_MAX>();
+    if constexpr (N <= 512 && Plan16B<N>::HAS) e |= prep_tma<N, 1, 1>();
     return e;
 }
 
@@ -107,7 +108,9 @@ template <int N>
 static int units_tma1(const PassArgs &a) { return a.kxn * (a.n2 / 16); }
 
 // The TMA-staged P2 / P4 of one launch's items: maps over each item's buf1
-// (P2) or buf0 and buf1 (P4) as [(n0 + 1) rows1][n2] complex.
+// (P2) or buf0 and buf1 (P4) as [(n0 + 1) rows1][n2] complex.  Variant bits:
+// 2 = one CTA per SM; 8 = the second radix split (single solves, lengths
+// that have one).
 template <int N, class Wk>
 static int tma_launch1(int kind, const Wk &w, int flag, int var, cudaStream_t st)
 {
@@ -131,11 +134,18 @@ static int tma_launch1(int kind, const Wk &w, int flag, int var, cudaStream_t st
     }
     const int total = w.offs[w.nitems];
     const int sms = sm_count();
-    if (kind == PASS_P2F)
-        return launch_pdl(p2_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc1<N, MAXI>::p2)), C::THREADS,
-                          smem_p2_tma<N>(), st, w, m);
-    return launch_pdl(p4_tma<N, MAXI>, std::min(total, sms * ((var & 2) ? 1 : TmaOcc1<N, MAXI>::p4)), C::THREADS,
-                      smem_p4_tma<N>(), st, w, m, flag);
+    auto go = [&](auto alt) {
+        constexpr int ALT = decltype(alt)::value;
+        using O = TmaOcc1<N, MAXI, ALT>;
+        if (kind == PASS_P2F)
+            return launch_pdl(p2_tma<N, MAXI, ALT>, std::min(total, sms * ((var & 2) ? 1 : O::p2)), C::THREADS,
+                              smem_p2_tma<N>(), st, w, m);
+        return launch_pdl(p4_tma<N, MAXI, ALT>, std::min(total, sms * ((var & 2) ? 1 : O::p4)), C::THREADS,
+                          smem_p4_tma<N>(), st, w, m, flag);
+    };
+    if constexpr (MAXI == 1 && Plan16B<N>::HAS)
+        if (var & 8) return go(std::integral_constant<int, 1>{});
+    return go(std::integral_constant<int, 0>{});
 }
 
 int prepare_axis1(int N)

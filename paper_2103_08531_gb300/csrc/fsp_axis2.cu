@@ -27,7 +27,7 @@ int supported_axis2(int N)
 
 template <int N, int MAXI>
 struct Occ2 {
-    static inline int p3 = 1, p3a = 1, p3one = 1, wide = 1;
+    static inline int p3 = 1, p3a = 1, p3one = 1, p3oneB = 1, wide = 1;
 };
 
 // Lines of 1024 and 2048 points: the multi-warp-per-line middle pass
@@ -47,6 +47,12 @@ static int prep_one()
             int b1 = 0;
             e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p3_fwd1<N>, C::THREADS, C::SMEM);
             Occ2<N, MAXI>::p3one = std::max(1, b1);
+            if constexpr (Plan16B<N>::HAS) {
+                using CB = WarpCfg<N, 1>;
+                e |= cudaFuncSetAttribute(p3_fwd1<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CB::SMEM);
+                e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, p3_fwd1<N, 1>, CB::THREADS, CB::SMEM);
+                Occ2<N, MAXI>::p3oneB = std::max(1, b1);
+            }
         }
         e |= cudaFuncSetAttribute(p3_adj<N, MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         int b = 0, ba = 0;
@@ -126,8 +132,17 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
         if constexpr (N <= 512) {
             using C = WarpCfg<N>;
             const int ctas = (total + C::WARPS - 1) / C::WARPS;
-            // variant bit 2: one CTA per SM (else as many as fit)
+            // variant bit 2: one CTA per SM (else as many as fit); bit 8 (single
+            // solves): the second radix split of the length
             const bool one = (var & 2) != 0;
+            constexpr int AB = Plan16B<N>::HAS ? 1 : 0;   // (keeps the branch below well-formed for every N)
+            if constexpr (AB && MAXI == 1 && FSP_P3_ONE) {
+                using CB = WarpCfg<N, AB>;
+                if (kind == PASS_P3F && (var & 8))
+                    return launch_pdl(p3_fwd1<N, AB>, std::min((total + CB::WARPS - 1) / CB::WARPS,
+                                                              cap_sm * (one ? 1 : Occ2<N, MAXI>::p3oneB)),
+                                      CB::THREADS, CB::SMEM, st, w.item[0], flag);
+            }
             if (kind == PASS_P3F && MAXI == 1 && FSP_P3_ONE)
                 return launch_pdl(p3_fwd1<N>, std::min(ctas, cap_sm * (one ? 1 : Occ2<N, MAXI>::p3one)), C::THREADS,
                                   C::SMEM, st, w.item[0], flag);
@@ -152,6 +167,16 @@ static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaSt
         }
         return (int)cudaGetLastError();
     });
+}
+
+int has_radix_plan_b(int N)
+{
+    switch (N) {
+#define X(n) case n: return Plan16B<n>::HAS ? 1 : 0;
+        FSP_AXIS2_SIZES(X)
+#undef X
+    default: return 0;
+    }
 }
 
 int launch_axis2(int kind, int N, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
@@ -188,11 +213,25 @@ int make_twiddles_gall(float2 *tw, int N, cudaStream_t st)
     }
 }
 
+// Gathered blocks of Plan16<N> after the N-entry table, then those of
+// Plan16B<N> where the length has a second radix split.
+template <int N>
+static int fill_aux(float2 *tw, cudaStream_t st)
+{
+    k_twiddles_aux<N, typename Plan16<N>::R><<<4, 256, 0, st>>>(tw);
+    if constexpr (Plan16B<N>::HAS) {
+        static_assert(AuxEnd<1, AuxOff<N, 1>::value, typename Plan16B<N>::R>::value <= TW_AUX,
+                      "both plans' gathered blocks must fit the table's spare entries");
+        k_twiddles_aux<N, typename Plan16B<N>::R, AuxOff<N, 1>::value><<<4, 256, 0, st>>>(tw);
+    }
+    return (int)cudaGetLastError();
+}
+
 int make_twiddles_aux(float2 *tw, int N, cudaStream_t st)
 {
     switch (N) {
 #define X(n) \
-    case n: k_twiddles_aux<n, typename Plan16<n>::R><<<4, 256, 0, st>>>(tw); return (int)cudaGetLastError();
+    case n: return fill_aux<n>(tw, st);
         X(32) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
 #undef X
     default: return 0;   // block-mode lengths use the main table only

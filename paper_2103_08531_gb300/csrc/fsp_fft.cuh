@@ -536,10 +536,13 @@ struct Passes<N, E, INV, NS, Radices<R, RS...>, SYNC, TW, OFF> {
 // Whole-line transform.  Precondition: every thread of the sync group (block
 // or warp) calls it and nobody still reads the shared buffer.  On return the
 // shared buffer is free again.
-template <int N, int E, bool INV, bool PRUNE_IN, class RAD, class View, int SYNC = SYNC_BLOCK, int TW = TW_TABLE>
+// OFF: where the plan's gathered twiddle blocks start after the N-entry table
+// (TW_GATHER / TW_SMEM; 0 for the first plan of a length).
+template <int N, int E, bool INV, bool PRUNE_IN, class RAD, class View, int SYNC = SYNC_BLOCK, int TW = TW_TABLE,
+          int OFF = 0>
 __device__ __forceinline__ void line_fft(float2 (&v)[E], int j, const float2 *__restrict__ tw, const View &sm)
 {
-    Passes<N, E, INV, 1, RAD, SYNC, TW>::template run<PRUNE_IN>(v, j, tw, sm);
+    Passes<N, E, INV, 1, RAD, SYNC, TW, OFF>::template run<PRUNE_IN>(v, j, tw, sm);
 }
 
 // Gathered twiddle blocks for a radix plan: for every pass with 1 < NS < 32,
@@ -602,10 +605,10 @@ __global__ void k_twiddles_gall(float2 *tw)
         AuxFillAll<N, 1, 0, RAD>::run(tw + N, i);
 }
 
-template <int N, class RAD>
+template <int N, class RAD, int OFF = 0>
 __global__ void k_twiddles_aux(float2 *tw)
 {
-    AuxFill<N, 1, 0, RAD>::run(tw + N, blockIdx.x * blockDim.x + threadIdx.x);
+    AuxFill<N, 1, OFF, RAD>::run(tw + N, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Radix plans per padded length for block-synchronous tiles (E values per thread).
@@ -636,6 +639,34 @@ template <> struct Plan16<192> { static constexpr int E = 12; using R = Radices<
 template <> struct Plan16<256> { static constexpr int E = 16; using R = Radices<16, 16>; };
 template <> struct Plan16<384> { static constexpr int E = 12; using R = Radices<4, 4, 4, 2, 3>; };
 template <> struct Plan16<512> { static constexpr int E = 16; using R = Radices<16, 16, 2>; };
+
+// A second radix split of the same lengths with the same values per thread,
+// the alternative a tuned launch variant can pick (variant bit 8): radix 8
+// first, so the pruned first pass and every exchange move other strides.
+template <int N>
+struct Plan16B {
+    static constexpr bool HAS = false;
+};
+template <> struct Plan16B<128> { static constexpr bool HAS = true; static constexpr int E = 16; using R = Radices<8, 16>; };
+template <> struct Plan16B<256> { static constexpr bool HAS = true; static constexpr int E = 16; using R = Radices<8, 8, 4>; };
+template <> struct Plan16B<512> { static constexpr bool HAS = true; static constexpr int E = 16; using R = Radices<8, 8, 8>; };
+
+// The plan of a length: ALT = 0 Plan16, ALT = 1 Plan16B.
+template <int N, int ALT>
+struct PlanSel {
+    using type = Plan16<N>;
+};
+template <int N>
+struct PlanSel<N, 1> {
+    using type = Plan16B<N>;
+};
+
+// Gathered twiddle blocks of Plan16B<N> start where those of Plan16<N> end
+// (offsets after the N-entry table; the first plan's blocks start at 0).
+template <int N, int ALT>
+struct AuxOff {
+    static constexpr int value = ALT ? AuxEnd<1, 0, typename Plan16<N>::R>::value : 0;
+};
 
 
 } // namespace fsp

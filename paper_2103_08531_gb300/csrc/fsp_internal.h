@@ -50,6 +50,7 @@ int make_twiddles(float2 *tw, int N, cudaStream_t st);
 int make_twiddles_aux(float2 *tw, int N, cudaStream_t st);    // fsp_axis2.cu
 int make_twiddles_gall(float2 *tw, int N, cudaStream_t st);   // fsp_axis2.cu
 int twiddle_gall_entries(int N);                              // fsp_axis2.cu
+int has_radix_plan_b(int N);   // 1: length N has a second radix split (Plan16B), fsp_axis2.cu
 constexpr int TW_AUX = 1024;   // gathered-twiddle entries after each N-entry table (N <= 512)
 inline size_t twiddle_entries(int N)
 {

@@ -875,15 +875,20 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_pst(const __grid_co
 #ifndef FSP_TILE_C
 #define FSP_TILE_C 16
 #endif
-template <int N, int EE>
+template <int N, int EE, int ALT = 0>
 struct TilePlan {
     static constexpr int E = Plan16<N>::E;
     using R = typename Plan16<N>::R;
 };
 template <int N>
-struct TilePlan<N, 8> {
+struct TilePlan<N, 8, 0> {
     static constexpr int E = Plan1D<N>::E;
     using R = typename Plan1D<N>::R;
+};
+template <int N>
+struct TilePlan<N, 16, 1> {
+    static constexpr int E = Plan16B<N>::E;
+    using R = typename Plan16B<N>::R;
 };
 
 // Twiddle source of the column tiles: a copy of the table in shared memory
@@ -892,14 +897,15 @@ struct TilePlan<N, 8> {
 #define FSP_TILE_TW TW_STABLE
 #endif
 
-// EE = 16: 16 values per thread (Plan16); EE = 8: Plan1D (8 per thread, 12 for 192).
-template <int N, int EE = 16>
+// EE = 16: 16 values per thread (Plan16, or Plan16B with ALT = 1); EE = 8:
+// Plan1D (8 per thread, 12 for 192).
+template <int N, int EE = 16, int ALT = 0>
 struct TileCfg {
-    static constexpr int E = TilePlan<N, EE>::E;
+    static constexpr int E = TilePlan<N, EE, ALT>::E;
     static constexpr int T = N / E;
     static constexpr int C = FSP_TILE_C;           // columns per tile (complex)
     static constexpr int THREADS = T * C;
-    using RAD = typename TilePlan<N, EE>::R;
+    using RAD = typename TilePlan<N, EE, ALT>::R;
     static constexpr int TWS = FSP_TILE_TW == TW_STABLE ? N : 0;
     // exchange buffer (N x C), then the twiddle copy; the last region of
     // every tile kernel's shared memory, in float2
@@ -1360,23 +1366,26 @@ __global__ void __launch_bounds__(TileCfg<N>::THREADS) p2_adj_t(const __grid_con
 #else
 #define FSP_P3_BOUNDS(t) __launch_bounds__(t)
 #endif
-template <int N>
-using P3Plan = Plan16<N>;
+// ALT = 1: the second radix split (Plan16B; tuned variant bit 8), whose
+// gathered twiddle blocks follow those of the first in the same table.
+template <int N, int ALT = 0>
+using P3Plan = typename PlanSel<N, ALT>::type;
 
-template <int N>
+template <int N, int ALT = 0>
 struct WarpCfg {
-    static constexpr int E = P3Plan<N>::E;
+    static constexpr int E = P3Plan<N, ALT>::E;
     static constexpr int T = N / E;
     static constexpr int LPW = 32 / T;     // lines per warp
     static constexpr int WARPS = 4;
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int PAD = 4;
     static constexpr int SPAN = RowSpan<N, PAD>::value;
-    using RAD = typename P3Plan<N>::R;
+    using RAD = typename P3Plan<N, ALT>::R;
+    static constexpr int OFF = AuxOff<N, ALT>::value;   // the plan's gathered blocks after the table
     static constexpr int RL = SPAN;             // shared memory per line (exchange buffer)
     // TW_SMEM: the twiddle table (main part and gathered blocks) after the lines
     static constexpr int TWOFF = RL * LPW * WARPS;
-    static constexpr int TWS = FSP_P3_TW == TW_SMEM ? AuxEnd<1, N, RAD>::value : 0;
+    static constexpr int TWS = FSP_P3_TW == TW_SMEM ? AuxEnd<1, N + OFF, RAD>::value : 0;
     static constexpr size_t SMEM = (size_t)(TWOFF + TWS) * sizeof(float2);
     // With TW_SMEM: copy the table into shared memory (every thread of the
     // block calls this once, before its first transform) and return the copy.
@@ -1471,10 +1480,10 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd(const __grid_constant_
 
 // Single-solve forward middle pass (the arguments by value; same arithmetic
 // as p3_fwd below, kept separate because its register allocation is smaller).
-template <int N>
+template <int N, int ALT = 0>
 __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE)
 {
-    using C = WarpCfg<N>;
+    using C = WarpCfg<N, ALT>;
     constexpr int E = C::E, T = C::T, LPW = C::LPW;
     // the launcher runs length N on lines of n2 = N / 2 cells; a compile-time
     // n2 turns the wavenumber and kernel-octant index arithmetic into constants
@@ -1517,7 +1526,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
         fetch(g + gstride);
         const int kx = pow2 ? lc >> rsh : lc / a.rows1;
         const int row = pow2 ? lc & (a.rows1 - 1) : lc % a.rows1;
-        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
+        line_fft<N, E, false, true, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW, C::OFF>(v, j, tw, sm);
         const float *Kr = krow(a, kx, row);
         float2 u[E];
 #pragma unroll
@@ -1528,14 +1537,14 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
             const float kk = wave(k, n2, a.k2s);
             u[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
         }
-        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(v, j, tw, sm);
+        line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW, C::OFF>(v, j, tw, sm);
         if (act) {
             float2 *L0 = a.buf0 + (size_t)lc * n2;
 #pragma unroll
             for (int r = 0; r < E / 2; ++r) L0[j + r * T] = v[r];
         }
         if (withE) {
-            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW>(u, j, tw, sm);
+            line_fft<N, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, FSP_P3_TW, C::OFF>(u, j, tw, sm);
             if (act) {
                 float2 *L1 = a.buf1 + (size_t)lc * n2;
 #pragma unroll

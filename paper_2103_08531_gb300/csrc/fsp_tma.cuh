@@ -169,7 +169,8 @@ __device__ __forceinline__ bool tma_tile_failed(bool ok, uint64_t *bar, unsigned
 // p2_fwd, p4_fwd, p5_fwd: column = tid % 16, line thread j = tid / 16,
 // block-synchronous transforms through the [position][16] exchange buffer);
 // only the staging differs.  After the block barrier that ends the reads of a
-// stage, thread 0 issues the next tile's copies into it.
+// stage, thread 0 issues the next tile's copies into it.  ALT = 1 transforms
+// with the second radix split of the length (Plan16B, tuned variant bit 8).
 
 template <int MAXI>
 struct TmaBatch {
@@ -179,11 +180,11 @@ struct TmaBatch {
 // P1: rho column pairs (z, z + 1) of a tile of 32 reals -> half spectrum in
 // k0, rows 0 .. n1 - 1 of buf1 (3D) or buf0 (2D).  Unit: (y, tile).  Map 0:
 // rho as [n0][n1][n2] floats, box 32 x 1 x N/2.
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_constant__ Work<MAXI> W,
                                                                   const __grid_constant__ TmaBatch<MAXI> maps)
 {
-    using C = TileCfg<N, 16>;
+    using C = TileCfg<N, 16, ALT>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];
@@ -242,11 +243,11 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p1_tma(const __grid_c
 // P2: buf1 rows 0 .. n1 - 1 -> forward axis 1 -> buf0 rows 0 .. 2 n1 - 1.
 // Unit: (k0, tile) over planes [kx0, kx0 + kxn).  Map 0: buf1 as
 // [(n0 + 1) rows1][n2] complex, box 16 x N/2.
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_constant__ Work<MAXI> W,
                                                                   const __grid_constant__ TmaBatch<MAXI> maps)
 {
-    using C = TileCfg<N, 16>;
+    using C = TileCfg<N, 16, ALT>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];
@@ -288,11 +289,11 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p2_tma(const __grid_c
 // P4: buf0 (phi stream, 2 n1 rows) -> rows [0, n1) phi, rows [n1, 2 n1) -i k1 phi;
 // buf1 (E2 stream) -> rows [0, n1).  Unit: (k0, tile) over planes [kx0, kx0 + kxn).
 // Maps 0 and 1: buf0 and buf1 as [(n0 + 1) rows1][n2] complex, box 16 x min(N, 256).
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_constant__ Work<MAXI> W,
                                                                   const __grid_constant__ TmaBatch<MAXI> maps, int withE)
 {
-    using C = TileCfg<N, 16>;
+    using C = TileCfg<N, 16, ALT>;
     constexpr int E = C::E, T = C::T;
     constexpr int BOXR = N < 256 ? N : 256, NB = N / BOXR;
     using RAD = typename C::RAD;
@@ -359,11 +360,11 @@ __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p4_tma(const __grid_c
 // Stages: 0 the phi stream (buf0 row y), 1 the E1 stream (buf0 row n1 + y in
 // 3D, buf1 row y in 2D), 2 the E2 stream (buf1 row y, 3D).  Which streams an
 // item has follows its outputs.
-template <int N, int MAXI>
+template <int N, int MAXI, int ALT = 0>
 __global__ void __launch_bounds__(TileCfg<N, 16>::THREADS) p5_tma(const __grid_constant__ Work<MAXI> W,
                                                                   const __grid_constant__ TmaBatch<MAXI> maps)
 {
-    using C = TileCfg<N, 16>;
+    using C = TileCfg<N, 16, ALT>;
     constexpr int E = C::E, T = C::T, NH = N / 2;
     using RAD = typename C::RAD;
     extern __shared__ unsigned char smem_raw[];

@@ -3,8 +3,9 @@
     python -m paper_2103_08531_gb300.tune [--out PATH] [--mode 1|2]
 
 Each geometry's forward passes are timed in every launch variant the library
-offers for them (column-tile engine and values per thread, CTAs per SM, the
-middle-pass kernel for 1024- and 2048-point lines); the fastest variant per
+offers for them (column-tile engine and values per thread, the radix split of
+the transforms at 128, 256 and 512 points, CTAs per SM, the middle-pass kernel
+for 1024- to 8192-point lines); the fastest variant per
 (pass, padded length) is written to PATH, keyed by GPU architecture.  Mode 1
 keeps entries already in the file, mode 2 re-times everything.  Solves read the
 file through Plan.autotune(PATH, 0) or FSP_AUTOTUNE=cached FSP_TUNE_CACHE=PATH.

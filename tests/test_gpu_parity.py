@@ -445,6 +445,7 @@ def _write_cache(path, arch, shape, var_tile, var_p3):
 @pytest.mark.parametrize("shape,h", [((64, 64, 32), (0.02, 0.025, 0.03)), ((32, 128, 64), (0.03, 0.01, 0.02)),
                                      ((128, 64), (0.01, 0.02)), ((32, 64, 128), (0.03, 0.02, 0.01)),
                                      ((32, 32, 256), (0.03, 0.02, 0.005)), ((32, 32, 512), (0.03, 0.02, 0.004)),
+                                     ((256, 32, 32), (0.004, 0.03, 0.02)), ((32, 256, 32), (0.03, 0.004, 0.02)),
                                      ((32, 4096), (0.02, 0.0005)), ((4096, 32), (0.0005, 0.02))])
 def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
     """Each launch variant the autotuner can pick gives the oracle's answer."""
@@ -462,8 +463,10 @@ def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
         # block tiles with 16 / 8 values per thread, 6 / 7 those one CTA per SM
         # middle pass (bits 2 and, at 2n = 1024 / 2048, 4): the same bits of vt; at 2n = 8192
         # bit 4 takes the block-synchronous line kernel instead of the four-step pass, and for
-        # 8192-point columns (P5) the staged block kernel instead of the four-step through HBM
-        for vt, vp in [(0, 0), (2, 2), (4, 4), (5, 4), (6, 6), (7, 6)]:
+        # 8192-point columns (P5) the staged block kernel instead of the four-step through HBM;
+        # 8 / 10: the second radix split (8 x 16, 8 x 8 x 4, 8 x 8 x 8 at 2n = 128, 256, 512) in
+        # the TMA tiles and the middle pass, alone and one CTA per SM
+        for vt, vp in [(0, 0), (2, 2), (4, 4), (5, 4), (6, 6), (7, 6), (8, 8), (10, 10)]:
             _write_cache(path, arch, shape, vt, vp)
             plan.autotune(path, 0)
             assert fsp.tuned_variant("p1_fwd", 2 * shape[0]) == vt
