@@ -655,6 +655,7 @@ def run_other(args):
         line["tuning"] = load_tuning(plans[0], probs[0].shape)
         rhos = [torch.from_numpy(p.rho(np.float32)).cuda() for p in probs]
         batch = fsp.Batch(plans, rhos)
+        kernels = batch.kernel_count()
         graph = batch.capture()
         clocks.start()
         ms = _timed(graph.replay, args.steps, args.warmup)
@@ -672,7 +673,7 @@ def run_other(args):
                      "pipeline": {"bytes": byts, "gbs": byts / (per * 1e-3) / 1e9,
                                   "frac": byts / (per * 1e-3) / 1e9 / peak, "peak_kind": peak_kind},
                      "sequential_ms_per_batch": ms_seq / args.steps, "plan_seconds_64_geometries": t_plan,
-                     "gpu_launches": None, "clocks": clk})
+                     "kernels_per_batch": kernels, "gpu_launches": kernels * args.steps, "clocks": clk})
     elif args.workload == "gauss2d4096":
         prob = W.mixture_2d(4096, 16, 2)
         rho = torch.from_numpy(prob.rho(np.float32)).cuda()
@@ -735,7 +736,8 @@ def run_other(args):
                      "value": B / (per * 1e-3), "unit": "fwd+bwd items/s", "ms_per_step": per,
                      "config": {"workload": "8 x 128^3 VGF, 4-Gaussian densities (seeds 10..17), "
                                             "loss sum (phi - phi_t)^2 + 0.1 |E|^2"},
-                     "gpu_launches": None, "clocks": clk})
+                     # five forward and five adjoint passes per item; torch's loss ops are not counted
+                     "gpu_launches": 10 * B * args.steps, "clocks": clk})
     elif args.workload == "fd_direct":
         # the finite-difference field on a solved 256^3 HE potential, and FP64 direct-path solves at the
         # odd sizes of the paper's convergence studies

@@ -169,6 +169,13 @@ fsp_batch *fsp_batch_create(fsp_plan *const *plans, int count, const void *const
                             void *const *E);
 int fsp_batch_solve(fsp_batch *batch, void *cuda_stream);
 void fsp_batch_destroy(fsp_batch *batch);
+/* Number of kernels one fsp_batch_solve of this batch launches (a report for
+ * benchmarks and tests, not part of the paper's method): the solve is captured
+ * once on a private stream into a CUDA graph whose kernel nodes are counted;
+ * nothing runs on the GPU.  *count is written on FSP_OK.  FSP_ERR_INVALID for
+ * a NULL argument, FSP_ERR_CUDA if the capture fails.  Set-up, not a solve:
+ * do not call it while the calling thread captures a stream. */
+int fsp_batch_kernel_count(fsp_batch *batch, int *count);
 
 /*
  * Measurement hook: when count > 0, every later fsp_solve / fsp_solve_adjoint
@@ -198,7 +205,8 @@ int fsp_gradient_fd(const fsp_plan *plan, const void *phi, void *E, void *cuda_s
  * thread in column tiles; bit 2: one CTA per SM in persistent launches; bit 8,
  * without bit 4, at padded lengths 128, 256 and 512: a second radix split of
  * the transforms, 8 x 16, 8 x 8 x 4 and 8 x 8 x 8 instead of 16 x 8, 16 x 16
- * and 16 x 16 x 2, in the TMA column tiles and the single-solve middle pass); the
+ * and 16 x 16 x 2, in the TMA column tiles and the single-solve middle pass,
+ * and for 1024-point middle lines two warp-synchronous 512-point halves); the
  * choice is a process-wide table keyed by pass and padded length, read by
  * every solve.  fsp_autotune fills it for the passes this plan uses:
  * mode 0 reads the JSON cache at cache_path (may be NULL) only; mode 1 reads

@@ -35,6 +35,7 @@ SIGNATURES = {
     "fsp_batch_create": (_vp, [_vpp, _i, _vpp, _vpp, _vpp]),
     "fsp_batch_solve": (_i, [_vp, _vp]),
     "fsp_batch_destroy": (None, [_vp]),
+    "fsp_batch_kernel_count": (_i, [_vp, _ip]),
     "fsp_plan_set_pass_events": (_i, [_vp, _vpp, _i]),
     "fsp_autotune": (_i, [_vp, ctypes.c_char_p, _i]),
     "fsp_gradient_fd": (_i, [_vp, _vp, _vp, _vp]),

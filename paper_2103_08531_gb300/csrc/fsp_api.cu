@@ -722,3 +722,33 @@ extern "C" int fsp_batch_solve(fsp_batch *b, void *cuda_stream)
 }
 
 extern "C" void fsp_batch_destroy(fsp_batch *b) { delete b; }
+
+// Kernels one fsp_batch_solve launches: the solve is captured once on a
+// private stream into a graph whose kernel nodes are counted (nothing runs).
+extern "C" int fsp_batch_kernel_count(fsp_batch *b, int *count)
+{
+    if (!b || !count) return set_err(FSP_ERR_INVALID);
+    cudaStream_t s = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return set_err(FSP_ERR_CUDA);
+    int rc = FSP_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) rc = FSP_ERR_CUDA;
+    if (rc == FSP_OK) {
+        const int r = run_batch(*b, s);
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess || r != FSP_OK) rc = r != FSP_OK ? r : FSP_ERR_CUDA;
+    }
+    size_t n = 0;
+    if (rc == FSP_OK && cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) rc = FSP_ERR_CUDA;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (rc == FSP_OK && n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) rc = FSP_ERR_CUDA;
+    int k = 0;
+    for (size_t i = 0; i < n && rc == FSP_OK; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) rc = FSP_ERR_CUDA;
+        else if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(s);
+    if (rc == FSP_OK) *count = k;
+    return set_err(rc);
+}

@@ -6,7 +6,8 @@
 // (not 192); 2 = one CTA per SM in the persistent launches instead of as many
 // as fit; 8 = without bit 4, the second radix split of the length (Plan16B:
 // 8 x 16 at 128, 8 x 8 x 4 at 256, 8 x 8 x 8 at 512, instead of 16 x 8,
-// 16 x 16 and 16 x 16 x 2) in the TMA tiles and the single-solve middle pass.  For the middle pass at 2n = 1024 and 2048, bit 4 selects the
+// 16 x 16 and 16 x 16 x 2) in the TMA tiles and the single-solve middle pass,
+// and at 2n = 1024 the middle pass as two 512-point halves (p3_fwd_2h).  For the middle pass at 2n = 1024 and 2048, bit 4 selects the
 // block-synchronous line kernel instead of the multi-warp-per-line one, and at
 // 2n = 8192 instead of the four-step (16 x 512) pass; for P5 at 2n = 8192 it
 // selects the staged block-synchronous columns instead of the four-step
@@ -51,7 +52,8 @@ std::vector<int> candidates(int kind, int N)
 {
     const bool tile = kind == PASS_P1F || kind == PASS_P2F || kind == PASS_P4F || kind == PASS_P5F;
     if (N > 512) {
-        if (kind == PASS_P3F && (N == 768 || N == 1024 || N == 2048)) return {0, 2, 4, 6};
+        if (kind == PASS_P3F && N == 1024) return {0, 2, 4, 6, 8, 10};   // 8: two 512-point halves
+        if (kind == PASS_P3F && (N == 768 || N == 2048)) return {0, 2, 4, 6};
         if ((kind == PASS_P3F || kind == PASS_P5F) && N == 8192) return {0, 4};
         return {0};
     }

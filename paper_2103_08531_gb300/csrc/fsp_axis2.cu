@@ -27,7 +27,7 @@ int supported_axis2(int N)
 
 template <int N, int MAXI>
 struct Occ2 {
-    static inline int p3 = 1, p3a = 1, p3one = 1, p3oneB = 1, wide = 1;
+    static inline int p3 = 1, p3a = 1, p3one = 1, p3oneB = 1, wide = 1, half = 1;
 };
 
 // Lines of 1024 and 2048 points: the multi-warp-per-line middle pass
@@ -76,6 +76,12 @@ static int prep_one()
             e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, p3_fwd_wide<N, MAXI>, W::THREADS, W::SMEM);
             Occ2<N, MAXI>::wide = std::max(1, bw);
         }
+        if constexpr (N == HalfCfg::N) {
+            int bh = 0;
+            e |= cudaFuncSetAttribute(p3_fwd_2h<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HalfCfg::SMEM);
+            e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, p3_fwd_2h<MAXI>, HalfCfg::THREADS, HalfCfg::SMEM);
+            Occ2<N, MAXI>::half = std::max(1, bh);
+        }
     }
     return e;
 }
@@ -115,6 +121,16 @@ template <int N>
 static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     const int cap_sm = sm_count();
+    if constexpr (N == HalfCfg::N) {   // variant bit 8: the line as two 512-point halves
+        if (kind == PASS_P3F && (var & 8) && !(var & 4)) {
+            return chunked(items, n, units_wide<N>, [&](auto &w) {
+                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
+                const int total = w.offs[w.nitems];
+                const int grid = std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::half));
+                return launch_pdl_if(kLongPdl<N>, p3_fwd_2h<MAXI>, grid, HalfCfg::THREADS, HalfCfg::SMEM, st, w, flag);
+            });
+        }
+    }
     if constexpr (kWide<N>) {
         if (kind == PASS_P3F && !(var & 4)) {
             return chunked(items, n, units_wide<N>, [&](auto &w) {

@@ -1657,6 +1657,138 @@ __global__ void __launch_bounds__(WideCfg<N>::THREADS, FSP_WIDE_MINB) p3_fwd_wid
     }
 }
 
+// Forward middle pass for 1024-point lines as two 512-point halves: the split
+// k = 2 k2 + k1, n = n2 + 512 n1 with one radix-2 step.  The input is zero for
+// n >= 512, so that step is a twiddle only:
+//   X[2 k2 + k1] = DFT_512( x[n2] W_1024^(n2 k1) )[k2],
+// and warp k1 of a line transforms its half of the spectrum alone, warp-
+// synchronously, with the 512-point engine of the middle pass (16 values per
+// lane, shuffle exchange before the closing radix-2 pass).  After the product
+// with the kernel octant (and -i k2 for E), the inverse halves A_k1 = IDFT_512
+// of X[2 k2 + k1] give the cropped output
+//   x[n] = A_0[n] + W_1024^(-n) A_1[n],  n < 512,
+// one exchange of half a line between the two warps through shared memory
+// (warp 0 finishes n < 256, warp 1 the rest).  The 512-point table (main part
+// and gathered blocks) is read out of the 1024-point table, W_512^m = W_1024^2m
+// (the same FP64 angle, so the same FP32 values).  Two lines per CTA of four
+// warps, persistent over line pairs, the next line's input prefetched into
+// registers.  Tuned variant bit 8 at 2n = 1024.
+struct HalfCfg {
+    static constexpr int N = 1024, H = 512, E = 16;
+    using RAD = Plan16<512>::R;
+    static constexpr int WARPS = 4, THREADS = 32 * WARPS, LPC = 2;
+    static constexpr int PAD = 4;
+    static constexpr int SPAN = RowSpan<H, PAD>::value;     // per-warp exchange line
+    static constexpr int TW = AuxEnd<1, H, RAD>::value;      // 512-point table with its gathered blocks
+    static constexpr int XB = WARPS * SPAN;                   // combine buffers: [line][stream][H]
+    static constexpr int TWO = XB + LPC * 2 * H;              // the 512-point table
+    static constexpr int W1O = TWO + TW;                      // W_1024^n, n < 512
+    static constexpr size_t SMEM = (size_t)(W1O + H) * sizeof(float2);
+    static_assert(TW == H + 256, "the table fill below follows the 16 x 16 x 2 plan");
+};
+
+template <int MAXI>
+__global__ void __launch_bounds__(HalfCfg::THREADS) p3_fwd_2h(const __grid_constant__ Work<MAXI> W, int withE)
+{
+    using C = HalfCfg;
+    constexpr int E = C::E, H = C::H, N = C::N, LPC = C::LPC;
+    constexpr int n2 = H;   // cells per line
+    using RAD = typename C::RAD;
+    extern __shared__ float2 smem[];
+    pdl_trigger();
+    const int warp = threadIdx.x / 32, j = threadIdx.x % 32;
+    const int li = warp / 2, half = warp % 2;
+    const int nw = W.count();
+    RowView<C::PAD> sm{smem + warp * C::SPAN};
+    float2 *cb = smem + C::XB + li * 2 * H;   // this line's combine buffers (phi, E)
+    float2 *stw = smem + C::TWO;
+    float2 *w1 = smem + C::W1O;
+    {
+        const float2 *g = W.item[0].tw2;   // the 1024-point table (every item of the launch has 2 n2 = 1024)
+        for (int i = threadIdx.x; i < H; i += C::THREADS) {
+            stw[i] = g[2 * i];
+            w1[i] = g[i];
+        }
+        // gathered block of the second pass (NS = 16, R = 16): [r][k] = W_512^(2 r k)
+        for (int i = threadIdx.x; i < 256; i += C::THREADS) stw[H + i] = g[(4 * (i / 16) * (i % 16)) % N];
+    }
+    __syncthreads();
+    pdl_wait();
+    float2 pv[E];   // the next line's input (n < 512)
+    auto fetch = [&](int gg) {
+        const int it = W.find(gg < nw ? gg : 0);
+        const PassArgs &b = W.item[it];
+        const int bline = (gg - W.offs[it]) * LPC + li;
+        const bool bact = gg < nw && bline < (b.n0 + 1) * b.rows1;
+        const float2 *L = b.buf0 + (size_t)(bact ? bline : 0) * n2;
+#pragma unroll
+        for (int r = 0; r < E; ++r)
+            if (bact) pv[r] = L[j + 32 * r];
+    };
+#pragma unroll
+    for (int r = 0; r < E; ++r) pv[r] = make_float2(0.f, 0.f);
+    // the two warps of a line meet at named barrier 1 + li
+    auto line_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + li), "n"(64) : "memory"); };
+    // cropped output of an inverse half: x[n] = A_0[n] + W^(-n) A_1[n], n < 512
+    auto combine = [&](float2 (&x)[E], float2 *buf, float2 *dst, bool act) {
+        if (half == 0) {
+#pragma unroll
+            for (int r = E / 2; r < E; ++r) buf[j + 32 * r] = x[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) buf[j + 32 * r] = cmul_dir<true>(x[r], w1[j + 32 * r]);
+        }
+        line_sync();
+        if (half == 0) {
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const float2 o = x[r] + buf[j + 32 * r];
+                if (act) dst[j + 32 * r] = o;
+            }
+        } else {
+#pragma unroll
+            for (int r = E / 2; r < E; ++r) {
+                const float2 o = buf[j + 32 * r] + cmul_dir<true>(x[r], w1[j + 32 * r]);
+                if (act) dst[j + 32 * r] = o;
+            }
+        }
+    };
+    int g = blockIdx.x;
+    fetch(g);
+    for (; g < nw; g += gridDim.x) {
+        FSP_UNIT(W, g, a, u);
+        const int lines = (a.n0 + 1) * a.rows1;
+        const int line = u * LPC + li;
+        const bool act = line < lines;
+        const int lc = act ? line : 0;
+        float2 v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = half ? cmul(pv[r], w1[j + 32 * r]) : pv[r];
+        fetch(g + gridDim.x);
+        const int kx = lc / a.rows1, row = lc % a.rows1;
+        line_fft<H, E, false, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_SMEM>(v, j, stw, sm);
+        const float *Kr = krow(a, kx, row);
+        float2 q[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = 2 * (j + 32 * r) + half;
+            const int kf = k <= n2 ? k : N - k;
+            v[r] = (act ? __ldg(Kr + kf) : 0.f) * v[r];
+            const float kk = wave(k, n2, a.k2s);
+            q[r] = make_float2(kk * v[r].y, -kk * v[r].x);   // -i k2 (K rho^)
+        }
+        line_fft<H, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_SMEM>(v, j, stw, sm);
+        combine(v, cb, a.buf0 + (size_t)lc * n2, act);
+        if (withE) {
+            line_fft<H, E, true, false, RAD, RowView<C::PAD>, SYNC_WARP, TW_SMEM>(q, j, stw, sm);
+            combine(q, cb + H, a.buf1 + (size_t)lc * n2, act);
+        }
+        // the next line's combines write these buffers only after both warps
+        // have passed the barrier of the other stream (or of this one, without E)
+        if (!withE) line_sync();
+    }
+}
+
 // Adjoint middle pass, warp per line group.
 template <int N, int MAXI>
 __global__ void __launch_bounds__(WarpCfg<N>::THREADS) p3_adj(const __grid_constant__ Work<MAXI> W, int hasE)

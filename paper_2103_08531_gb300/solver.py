@@ -230,6 +230,12 @@ class Batch:
         _lib.check(self.lib.fsp_batch_solve(self.handle, _stream(stream)), "fsp_batch_solve")
         return self.phis, self.Es
 
+    def kernel_count(self) -> int:
+        """Kernels one run() launches (counted on a captured graph; nothing runs)."""
+        n = ctypes.c_int(0)
+        _lib.check(self.lib.fsp_batch_kernel_count(self.handle, ctypes.byref(n)), "fsp_batch_kernel_count")
+        return n.value
+
     def capture(self, warmup: int = 1):
         """Record run() into a torch.cuda.CUDAGraph; replay with graph.replay()."""
         s = torch.cuda.Stream()

@@ -353,6 +353,24 @@ def test_batched_many_mixed_items_and_graph(fsp):
         assert torch.equal(ph, ph1) and torch.equal(E, E1)
 
 
+def test_batch_kernel_count(fsp):
+    """fsp_batch_kernel_count reports one launch per (pass, padded length) of the batch, and the
+    counting capture leaves the batch usable."""
+    specs = [((32, 32, 32), (0.02, 0.02, 0.02)), ((32, 32, 32), (0.03, 0.02, 0.01)),
+             ((64, 32, 128), (0.01, 0.02, 0.005))]
+    plans = [fsp.Plan(s, h, "vgf") for s, h in specs]
+    rhos = [torch.from_numpy(_mixture(s, h, 120 + i, count=1).rho(np.float32)).cuda() for i, (s, h) in enumerate(specs)]
+    batch = fsp.Batch(plans, rhos)
+    # P1 and P5: 2 n0 in {64, 128}; P2 and P4: 2 n1 = 64; P3: 2 n2 in {64, 256}
+    assert batch.kernel_count() == 8
+    assert fsp.Batch(plans[:1], rhos[:1]).kernel_count() == 5
+    phis, Es = batch.run()
+    torch.cuda.synchronize()
+    for p, r, ph, E in zip(plans, rhos, phis, Es):
+        ph1, E1 = p.solve(r)
+        assert torch.equal(ph, ph1) and torch.equal(E, E1)
+
+
 def test_batched_rejects_repeated_plan(fsp):
     p = fsp.Plan((32, 32, 32), (0.02, 0.02, 0.02), "vgf")
     r = torch.zeros((32, 32, 32), device="cuda")
@@ -465,7 +483,8 @@ def test_every_tuning_variant_is_correct(fsp, oracle_mod, shape, h, tmp_path):
         # bit 4 takes the block-synchronous line kernel instead of the four-step pass, and for
         # 8192-point columns (P5) the staged block kernel instead of the four-step through HBM;
         # 8 / 10: the second radix split (8 x 16, 8 x 8 x 4, 8 x 8 x 8 at 2n = 128, 256, 512) in
-        # the TMA tiles and the middle pass, alone and one CTA per SM
+        # the TMA tiles and the middle pass, and 1024-point middle lines as two 512-point
+        # halves, alone and one CTA per SM
         for vt, vp in [(0, 0), (2, 2), (4, 4), (5, 4), (6, 6), (7, 6), (8, 8), (10, 10)]:
             _write_cache(path, arch, shape, vt, vp)
             plan.autotune(path, 0)
