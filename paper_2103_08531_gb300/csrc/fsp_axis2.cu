@@ -76,7 +76,7 @@ static int prep_one()
             e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, p3_fwd_wide<N, MAXI>, W::THREADS, W::SMEM);
             Occ2<N, MAXI>::wide = std::max(1, bw);
         }
-        if constexpr (N == HalfCfg::N) {
+        if constexpr (N == HalfCfg::N && MAXI == 1) {   // single solves only (batches keep the defaults)
             int bh = 0;
             e |= cudaFuncSetAttribute(p3_fwd_2h<MAXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HalfCfg::SMEM);
             e |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, p3_fwd_2h<MAXI>, HalfCfg::THREADS, HalfCfg::SMEM);
@@ -121,14 +121,11 @@ template <int N>
 static int run(int kind, const PassArgs *items, int n, int flag, int var, cudaStream_t st)
 {
     const int cap_sm = sm_count();
-    if constexpr (N == HalfCfg::N) {   // variant bit 8: the line as two 512-point halves
-        if (kind == PASS_P3F && (var & 8) && !(var & 4)) {
-            return chunked(items, n, units_wide<N>, [&](auto &w) {
-                constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
-                const int total = w.offs[w.nitems];
-                const int grid = std::min(total, cap_sm * ((var & 2) ? 1 : Occ2<N, MAXI>::half));
-                return launch_pdl_if(kLongPdl<N>, p3_fwd_2h<MAXI>, grid, HalfCfg::THREADS, HalfCfg::SMEM, st, w, flag);
-            });
+    if constexpr (N == HalfCfg::N) {   // variant bit 8 (single solves): the line as two 512-point halves
+        if (kind == PASS_P3F && (var & 8) && !(var & 4) && n == 1) {
+            Work<1> w = make_work<1>(items, 1, units_wide<N>);
+            const int grid = std::min(w.offs[1], cap_sm * ((var & 2) ? 1 : Occ2<N, 1>::half));
+            return launch_pdl_if(kLongPdl<N>, p3_fwd_2h<1>, grid, HalfCfg::THREADS, HalfCfg::SMEM, st, w, flag);
         }
     }
     if constexpr (kWide<N>) {
