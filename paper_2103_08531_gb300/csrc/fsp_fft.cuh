@@ -417,13 +417,13 @@ __device__ __forceinline__ void pair_exchange(float2 (&v)[E], const float2 *u, i
     const bool hi = (j & 16) != 0;
 #pragma unroll
     for (int i = 0; i < E / 2; ++i) {
-        // lo lanes keep u[2i] and send u[2i+1]; hi lanes keep u[2i+1] and send u[2i]
+        const float2 keep = hi ? u[2 * i + 1] : u[2 * i];
         const float2 send = hi ? u[2 * i] : u[2 * i + 1];
         float2 recv;
         recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
         recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
-        v[i] = hi ? recv : u[2 * i];
-        v[E / 2 + i] = hi ? u[2 * i + 1] : recv;
+        v[i] = hi ? recv : keep;
+        v[E / 2 + i] = hi ? keep : recv;
     }
 }
 
