@@ -292,6 +292,35 @@ int fsp_selftest_wait_timeout(double limit_seconds);
  */
 int fsp_plan_kernel_spectrum(const fsp_plan *plan, void *host_out, size_t bytes);
 
+/*
+ * Test hooks for the intermediates of the padded convolution (paper Sec. 1,
+ * the HE formula: pad, transform, product, inverse, crop, here one axis per
+ * pass).  fsp_plan_run_passes runs the first `passes` of a forward solve of
+ * rho (device, [nx][ny][nz]) on the plan's workspace, asynchronously on
+ * cuda_stream, and stops: 3D passes 1..4 of P1 (axis 0 pad + R2C), P2
+ * (axis 1 forward), P3 (axis 2 forward, product with the kernel spectrum and,
+ * with with_E, with -i k_2 too, inverse, crop), P4 (axis 1 inverse and crop,
+ * with with_E the -i k_1 stream); 2D passes 1..2 of P1 and P3.  The last pass
+ * (C2R to the outputs) is what fsp_solve adds.  Plane groups are not used.
+ * FSP_ERR_INVALID for a NULL or misaligned rho, a direct-path plan or passes
+ * outside that range; FSP_ERR_WORKSPACE without a large enough workspace.
+ *
+ * fsp_plan_workspace_layout: the two intermediate buffers of the workspace,
+ * buf0 at byte 0 and buf1 at *buf1_offset, each complex64 [dims[0]][dims[1]]
+ * [dims[2]] = [nx+1][2 ny][nz] (2D: [nx+1][1][ny]), last index fastest; the
+ * first index is k_0 of the half spectrum, the second the axis-1 position
+ * (frequency after P2, cell after P4; rows ny.. hold the -i k_1 stream after
+ * P4), the third the axis-2 position.  After P1 (3D) the spectrum of the
+ * padded axis 0 is in buf1 rows 0..ny-1 (2D: buf0); after P2 the axis-1
+ * spectrum is in buf0; after P3 the phi stream is in buf0 and the -i k_2
+ * stream in buf1; after P4 the phi stream is in buf0 rows 0..ny-1, the -i k_1
+ * stream in buf0 rows ny..2ny-1 and the -i k_2 stream in buf1 rows 0..ny-1.
+ * Values carry prod(h)/prod(2n) from the kernel spectrum from P3 on.
+ * FSP_ERR_INVALID for NULL arguments or a direct-path plan.
+ */
+int fsp_plan_run_passes(fsp_plan *plan, const void *rho, int passes, int with_E, void *cuda_stream);
+int fsp_plan_workspace_layout(const fsp_plan *plan, size_t *buf1_offset, int *dims);
+
 void fsp_plan_destroy(fsp_plan *plan);
 
 /*

@@ -41,6 +41,8 @@ SIGNATURES = {
     "fsp_gradient_fd": (_i, [_vp, _vp, _vp, _vp]),
     "fsp_tuned_variant": (_i, [_i, _i]),
     "fsp_plan_kernel_spectrum": (_i, [_vp, _vp, _sz]),
+    "fsp_plan_run_passes": (_i, [_vp, _vp, _i, _i, _vp]),
+    "fsp_plan_workspace_layout": (_i, [_vp, ctypes.POINTER(_sz), _ip]),
     "fsp_plan_destroy": (None, [_vp]),
     "fsp_solve_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "fsp_host_pipe_create": (_vp, [_vp, _i, _i, _i]),

@@ -384,6 +384,45 @@ static bool plane_groups_apply(const Plan &p)
            !(tuned_variant(PASS_P2F, 2 * p.n1) & 4) && !(tuned_variant(PASS_P4F, 2 * p.n1) & 4);
 }
 
+// The ungrouped forward schedule, passes 1 .. last of the plan's pass list
+// (3D: P1 .. P5; 2D: P1, P3, P5), with the pass events of the plan.
+static int run_plain_passes(const Plan &p, const PassArgs &a, int withE, int last, cudaStream_t st)
+{
+    const int N0 = 2 * p.n0, N1 = 2 * p.n1, N2 = 2 * p.n2;
+    int e = 0, m = 0, k = 0;   // k: passes run so far
+    mark(p, m++, st);
+    {
+        Range r("P1 axis 0 pad + R2C");
+        e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
+        ++k;
+    }
+    mark(p, m++, st);
+    if (!e && p.three_d && k < last) {
+        Range r("P2 axis 1 forward");
+        e = launch_axis1(PASS_P2F, N1, &a, 1, 0, tuned_variant(PASS_P2F, N1), st);
+        ++k;
+        mark(p, m++, st);
+    }
+    if (!e && k < last) {
+        Range r("P3 axis 2 forward, kernel product, inverse");
+        e = launch_axis2(PASS_P3F, N2, &a, 1, withE, tuned_variant(PASS_P3F, N2), st);
+        ++k;
+        mark(p, m++, st);
+    }
+    if (!e && p.three_d && k < last) {
+        Range r("P4 axis 1 inverse + crop");
+        e = launch_axis1(PASS_P4F, N1, &a, 1, withE, tuned_variant(PASS_P4F, N1), st);
+        ++k;
+        mark(p, m++, st);
+    }
+    if (!e && k < last) {
+        Range r("P5 axis 0 C2R + crop");
+        e = launch_axis0(PASS_P5F, N0, &a, 1, tuned_variant(PASS_P5F, N0), st);
+        mark(p, m++, st);
+    }
+    return e ? FSP_ERR_CUDA : FSP_OK;
+}
+
 // Forward pipeline for one plan on its workspace `ws`.
 int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E, cudaStream_t st)
 {
@@ -413,33 +452,7 @@ int run_forward(const Plan &p, void *ws, const float *rho, float *phi, float *E,
         mark(p, m++, st);
         return e ? FSP_ERR_CUDA : FSP_OK;
     }
-    mark(p, m++, st);
-    {
-        Range r("P1 axis 0 pad + R2C");
-        e = launch_axis0(PASS_P1F, N0, &a, 1, tuned_variant(PASS_P1F, N0), st);
-    }
-    mark(p, m++, st);
-    if (!e && p.three_d) {
-        Range r("P2 axis 1 forward");
-        e = launch_axis1(PASS_P2F, N1, &a, 1, 0, tuned_variant(PASS_P2F, N1), st);
-        mark(p, m++, st);
-    }
-    if (!e) {
-        Range r("P3 axis 2 forward, kernel product, inverse");
-        e = launch_axis2(PASS_P3F, N2, &a, 1, withE, tuned_variant(PASS_P3F, N2), st);
-    }
-    mark(p, m++, st);
-    if (!e && p.three_d) {
-        Range r("P4 axis 1 inverse + crop");
-        e = launch_axis1(PASS_P4F, N1, &a, 1, withE, tuned_variant(PASS_P4F, N1), st);
-        mark(p, m++, st);
-    }
-    if (!e) {
-        Range r("P5 axis 0 C2R + crop");
-        e = launch_axis0(PASS_P5F, N0, &a, 1, tuned_variant(PASS_P5F, N0), st);
-    }
-    mark(p, m++, st);
-    return e ? FSP_ERR_CUDA : FSP_OK;
+    return run_plain_passes(p, a, withE, p.three_d ? 5 : 3, st);
 }
 
 int run_adjoint(const Plan &p, void *ws, const float *g_phi, const float *g_E, float *g_rho, cudaStream_t st)
@@ -580,6 +593,28 @@ extern "C" int fsp_solve(fsp_plan *plan, const void *rho, void *phi, void *E, vo
     const Plan &p = plan->p;
     if (!p.ws || p.ws_bytes < per_solve_bytes(p, E != nullptr)) return set_err(FSP_ERR_WORKSPACE);
     return set_err(run_forward(p, p.ws, (const float *)rho, (float *)phi, (float *)E, (cudaStream_t)cuda_stream));
+}
+
+// Test hooks: the first passes of a forward solve, and where their results sit.
+extern "C" int fsp_plan_run_passes(fsp_plan *plan, const void *rho, int passes, int with_E, void *cuda_stream)
+{
+    if (!plan || !rho || !aligned16(rho)) return set_err(FSP_ERR_INVALID);
+    const Plan &p = plan->p;
+    if (p.direct || passes < 1 || passes >= (p.three_d ? 5 : 3)) return set_err(FSP_ERR_INVALID);
+    if (!p.ws || p.ws_bytes < per_solve_bytes(p, with_E != 0)) return set_err(FSP_ERR_WORKSPACE);
+    const PassArgs a = fwd_args(p, p.ws, (const float *)rho, nullptr, nullptr);
+    return set_err(run_plain_passes(p, a, with_E != 0, passes, (cudaStream_t)cuda_stream));
+}
+
+extern "C" int fsp_plan_workspace_layout(const fsp_plan *plan, size_t *buf1_offset, int *dims)
+{
+    if (!plan || !buf1_offset || !dims || plan->p.direct) return set_err(FSP_ERR_INVALID);
+    const Plan &p = plan->p;
+    *buf1_offset = align_up(p.buf_elems * sizeof(float2), 256);
+    dims[0] = p.n0 + 1;
+    dims[1] = p.rows1;
+    dims[2] = p.n2;
+    return set_err(FSP_OK);
 }
 
 extern "C" int fsp_solve_adjoint(fsp_plan *plan, const void *g_phi, const void *g_E, void *g_rho, void *cuda_stream)

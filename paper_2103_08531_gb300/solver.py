@@ -99,6 +99,22 @@ class Plan:
                    "fsp_plan_kernel_spectrum")
         return out
 
+    def intermediates(self, rho, passes: int, with_E: bool = True):
+        """Test hook: run the first `passes` forward passes on rho and return the
+        workspace's two intermediate buffers as complex64 tensors [nx+1][rows][nz]
+        (views of the workspace; see fsp_plan_run_passes in include/fsp.h)."""
+        off = ctypes.c_size_t(0)
+        dims = (ctypes.c_int * 3)()
+        _lib.check(self.lib.fsp_plan_workspace_layout(self.handle, ctypes.byref(off), dims), "fsp_plan_workspace_layout")
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.fsp_plan_run_passes(self.handle, _ptr(rho), int(passes), int(with_E), _stream()),
+                       "fsp_plan_run_passes")
+        n = dims[0] * dims[1] * dims[2]
+        shape = (dims[0], dims[1], dims[2])
+        b0 = self.workspace[:8 * n].view(torch.complex64).view(shape)
+        b1 = self.workspace[off.value:off.value + 8 * n].view(torch.complex64).view(shape)
+        return b0, b1
+
     def set_plane_group(self, planes: int):
         """Run the middle passes of single 3D solves in groups of `planes` k0 planes (0: off)."""
         _lib.check(self.lib.fsp_plan_set_plane_group(self.handle, int(planes)), "fsp_plan_set_plane_group")
