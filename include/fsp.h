@@ -77,8 +77,9 @@ enum fsp_status {
  *
  * Two solve paths.  The FFT passes (FP32) cover the padded lengths 2 n_a in
  * {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024} on every 3D axis and, in 2D,
- * also 2048, 4096 and 8192; the contiguous axis (nz in 3D, ny in 2D) needs a
- * cell count that is a multiple of 32.  Every other size
+ * also 1536, 2048, 3072, 4096, 6144 and 8192 (the powers of two and three times
+ * the powers of two); the contiguous axis (nz in 3D, ny in 2D) needs a cell
+ * count that is a multiple of 32.  Every other size
  * with 1 <= n_a <= 512, and every FSP_F64 plan, runs the direct-sum path: the
  * same pruned convolution with each 1D transform taken by its definition
  * (O(N^2) per line), in the plan's precision -- the paper's convergence

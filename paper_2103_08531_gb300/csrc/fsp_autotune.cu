@@ -34,7 +34,7 @@ using namespace fsp;
 
 namespace {
 
-const int kLengths[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 2048, 4096, 8192};
+const int kLengths[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192};
 constexpr int kNL = sizeof(kLengths) / sizeof(kLengths[0]);
 const char *kKindName[PASS_KINDS] = {"p1_fwd", "p1_adj", "p2_fwd", "p2_adj", "p3_fwd", "p3_adj", "p4_fwd", "p5_fwd"};
 
@@ -53,7 +53,7 @@ std::vector<int> candidates(int kind, int N)
     const bool tile = kind == PASS_P1F || kind == PASS_P2F || kind == PASS_P4F || kind == PASS_P5F;
     if (N > 512) {
         if (kind == PASS_P3F && N == 1024) return {0, 2, 4, 6, 8, 10};   // 8: two 512-point halves
-        if (kind == PASS_P3F && (N == 768 || N == 2048)) return {0, 2, 4, 6};
+        if (kind == PASS_P3F && (N == 768 || N == 1536 || N == 2048)) return {0, 2, 4, 6};
         if ((kind == PASS_P3F || kind == PASS_P5F) && N == 8192) return {0, 4};
         return {0};
     }

@@ -10,7 +10,8 @@
 
 namespace fsp {
 
-#define FSP_AXIS0_SIZES(X) X(32) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(2048) X(4096) X(8192)
+#define FSP_AXIS0_SIZES(X) \
+    X(32) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048) X(3072) X(4096) X(6144) X(8192)
 
 int supported_axis0(int N)
 {
@@ -22,7 +23,7 @@ int supported_axis0(int N)
     }
 }
 
-// 1: 2D first-axis passes with 2 n0 >= 2048 run persistent with a cp.async
+// 1: 2D first-axis passes with 2 n0 >= 1536 run persistent with a cp.async
 // stage (p1_fwd_pst / p5_fwd_pst); 0: one CTA per column group (p1_fwd_blk / p5_fwd_blk).
 #ifndef FSP_LONG_STAGED
 #define FSP_LONG_STAGED 1

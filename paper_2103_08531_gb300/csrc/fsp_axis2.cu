@@ -8,7 +8,8 @@
 
 namespace fsp {
 
-#define FSP_AXIS2_SIZES(X) X(64) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(2048) X(4096) X(8192)
+#define FSP_AXIS2_SIZES(X) \
+    X(64) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048) X(3072) X(4096) X(6144) X(8192)
 
 int supported_axis2(int N)
 {
@@ -30,10 +31,10 @@ struct Occ2 {
     static inline int p3 = 1, p3a = 1, p3one = 1, p3oneB = 1, wide = 1, half = 1;
 };
 
-// Lines of 1024 and 2048 points: the multi-warp-per-line middle pass
+// Lines of 768 to 2048 points: the multi-warp-per-line middle pass
 // (p3_fwd_wide) unless variant bit 4 asks for the block kernel.
 template <int N>
-constexpr bool kWide = N == 768 || N == 1024 || N == 2048;
+constexpr bool kWide = N == 768 || N == 1024 || N == 1536 || N == 2048;
 
 template <int N, int MAXI>
 static int prep_one()
@@ -209,7 +210,7 @@ int twiddle_gall_entries(int N)
 {
     switch (N) {
 #define X(n) case n: return AuxEndAll<1, 0, typename Plan1D<n>::R>::value;
-        X(768) X(1024) X(2048) X(4096) X(8192)
+        X(768) X(1024) X(1536) X(2048) X(4096) X(8192)
 #undef X
     default: return 0;
     }
@@ -220,7 +221,7 @@ int make_twiddles_gall(float2 *tw, int N, cudaStream_t st)
     switch (N) {
 #define X(n) \
     case n: k_twiddles_gall<n, typename Plan1D<n>::R><<<(n + 255) / 256, 256, 0, st>>>(tw); return (int)cudaGetLastError();
-        X(768) X(1024) X(2048) X(4096) X(8192)
+        X(768) X(1024) X(1536) X(2048) X(4096) X(8192)
 #undef X
     default: return 0;
     }

@@ -624,8 +624,11 @@ template <> struct Plan1D<384> { static constexpr int E = 12; using R = Radices<
 template <> struct Plan1D<512> { static constexpr int E = 8; using R = Radices<8, 8, 8>; };
 template <> struct Plan1D<768> { static constexpr int E = 12; using R = Radices<4, 4, 4, 4, 3>; };
 template <> struct Plan1D<1024> { static constexpr int E = 16; using R = Radices<16, 8, 8>; };
+template <> struct Plan1D<1536> { static constexpr int E = 12; using R = Radices<4, 4, 4, 4, 2, 3>; };
 template <> struct Plan1D<2048> { static constexpr int E = 16; using R = Radices<16, 16, 8>; };
+template <> struct Plan1D<3072> { static constexpr int E = 12; using R = Radices<4, 4, 4, 4, 4, 3>; };
 template <> struct Plan1D<4096> { static constexpr int E = 16; using R = Radices<16, 16, 16>; };
+template <> struct Plan1D<6144> { static constexpr int E = 12; using R = Radices<4, 4, 4, 4, 4, 2, 3>; };
 template <> struct Plan1D<8192> { static constexpr int E = 16; using R = Radices<16, 8, 8, 8>; };
 
 // Radix plans for 16-values-per-thread work (one warp or less per line).

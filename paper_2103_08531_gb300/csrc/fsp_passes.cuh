@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p5_fwd_blk(const __grid_co
 
 // ------------------------------- persistent staged passes for long columns
 //
-// 2D problems with 2 n0 >= 2048 hold only BZ = 2..8 columns of the first axis
+// 2D problems with 2 n0 >= 1536 hold only BZ = 2..8 columns of the first axis
 // per CTA, one CTA per SM.  These persistent versions copy the next column
 // group's input rows into a shared-memory stage with cp.async while the
 // current group is transformed, so the (narrow, row-strided) loads overlap
@@ -734,7 +734,7 @@ struct LongStage {
     }
 };
 
-// P1 (2D, 2 n0 >= 2048), persistent.  Unit: a group of BZ packed column pairs.
+// P1 (2D, 2 n0 >= 1536), persistent.  Unit: a group of BZ packed column pairs.
 template <int N, int MAXI>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_constant__ Work<MAXI> W)
 {
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) p1_fwd_pst(const __grid_co
     cp_async_wait_all();
 }
 
-// P5 (2D, 2 n0 >= 2048), persistent over (column group, stream) jobs: stream 0
+// P5 (2D, 2 n0 >= 1536), persistent over (column group, stream) jobs: stream 0
 // is buf0 -> (phi, E0) by W = (1 + k0) P, stream 1 is buf1 -> E1.  The next
 // job's rows are staged while the current job is transformed.
 template <int N, int MAXI>
@@ -1554,7 +1554,7 @@ __global__ void FSP_P3_BOUNDS(WarpCfg<N>::THREADS) p3_fwd1(PassArgs a, int withE
     }
 }
 
-// Forward middle pass for 1024- and 2048-point lines (2 n2 = 1024, 2048):
+// Forward middle pass for 768- to 2048-point lines (2 n2 = 768, 1024, 1536, 2048):
 // 16 values per thread, a line spread over N / 512 warps that synchronise
 // among themselves only (a named barrier per line), four warps per CTA,
 // persistent over line groups with the next line's input prefetched into

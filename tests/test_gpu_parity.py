@@ -119,7 +119,7 @@ LONG = [
 ]
 
 
-# padded lengths 32, 96, 384 and 768 (2^a 3^b) on the FFT passes, every axis role
+# padded lengths 32, 96, 384 and 768 (2^a 3^b) on the FFT passes, every axis role; 2D also 1536, 3072, 6144
 MIXED_LENGTHS = [
     ("n16_48_192", (16, 48, 192), (0.05, 0.03, 0.01), "vgf"),    # 2n = 32, 96, 384
     ("n384_48_64", (384, 48, 64), (0.004, 0.03, 0.02), "he"),    # 2n0 = 768 (block column tiles)
@@ -127,6 +127,12 @@ MIXED_LENGTHS = [
     ("n96_384_96", (96, 384, 96), (0.02, 0.004, 0.02), "vgf"),   # 2n1 = 768, 2n2 = 192
     ("2d_192_384", (192, 384), (0.01, 0.005), "vgf"),            # 2D: 384 columns, 768-point lines
     ("2d_48_96", (48, 96), (0.04, 0.02), "he"),                  # 2D: 96 columns
+    ("2d_768_32", (768, 32), (0.002, 0.03), "vgf"),              # 2D: 1536-point columns (staged, radix 3)
+    ("2d_32_768", (32, 768), (0.03, 0.002), "he"),               # 2D: 1536-point lines (four warps a line)
+    ("2d_1536_32", (1536, 32), (0.001, 0.03), "vgf"),            # 2D: 3072-point columns
+    ("2d_32_1536", (32, 1536), (0.03, 0.001), "vgf"),            # 2D: 3072-point lines (block kernel)
+    ("2d_3072_32", (3072, 32), (0.0006, 0.03), "he"),            # 2D: 6144-point columns
+    ("2d_32_3072", (32, 3072), (0.03, 0.0006), "vgf"),           # 2D: 6144-point lines
 ]
 
 
