@@ -118,6 +118,8 @@ static int prep()
     if constexpr (N <= 512) e |= prep_tma<N, 1>() | prep_tma<N, BATCH_MAX>();
     if constexpr (N <= 512 && Plan16B<N>::HAS) e |= prep_tma<N, 1, 1>();
     if constexpr (N == L4S::N) {
+        e |= cudaFuncSetAttribute(p5_4s_a<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P5A::SMEM);
+        e |= cudaFuncSetAttribute(p5_4s_a<BATCH_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P5A::SMEM);
         e |= cudaFuncSetAttribute(p5_4s_b<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_4s_b());
         e |= cudaFuncSetAttribute(p5_4s_b<BATCH_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p5_4s_b());
     }
@@ -168,7 +170,7 @@ static int run_p5_4s(const PassArgs *items, int n, cudaStream_t st)
             constexpr int MAXI = std::decay_t<decltype(w)>::max_items;
             const int total = w.offs[w.nitems];
             if (total == 0) return 0;
-            return launch_pdl(p5_4s_a<MAXI>, std::min(total, 8 * sm_count()), 256, 0, st, w, mode);
+            return launch_pdl(p5_4s_a<MAXI>, std::min(total, sm_count()), P5A::THREADS, P5A::SMEM, st, w, mode);
         });
     };
     auto step_b = [&](int mode) {

@@ -240,31 +240,65 @@ __global__ void __launch_bounds__(L4S::THREADS, 1) p3_fwd_4s(const __grid_consta
 // before mode 1.  No workspace beyond buf0 and buf1.
 
 // Step 1.  Unit: a block of 256 threads over (t in [0, 256], pair), pairs
-// fastest; mode 0 or 1 for the whole launch.
+// fastest; mode 0 or 1 for the whole launch.  Persistent; a thread's 16 input
+// rows of its next unit are copied (cp.async, 16 bytes each) into its own
+// slots of a two-buffer shared stage while the current unit is transformed:
+// the in-place stores of a unit never touch the rows of another unit.
+struct P5A {
+    static constexpr int THREADS = 256;
+    static constexpr size_t SMEM = (size_t)2 * 16 * THREADS * sizeof(float4);   // [buffer][row][thread]
+};
+
 template <int MAXI>
-__global__ void __launch_bounds__(256) p5_4s_a(const __grid_constant__ Work<MAXI> W, int mode)
+__global__ void __launch_bounds__(P5A::THREADS) p5_4s_a(const __grid_constant__ Work<MAXI> W, int mode)
 {
-    constexpr int N = L4S::N, NH = L4S::NH;
+    constexpr int N = L4S::N, NH = L4S::NH, TH = P5A::THREADS;
+    extern __shared__ float4 stg[];
     pdl_trigger();
     pdl_wait();
     const int nw = W.count();
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int tid = threadIdx.x;
+    // rows of unit w for this thread: 512 i + t (slot i) and 512 (i + 1) - t (slot 8 + i)
+    auto issue = [&](int w, int bsel) {
+        FSP_UNIT(W, w, b, ub);
+        const int pairs = b.n2 / 2;
+        const int idx = ub * TH + tid;
+        if (idx >= 257 * pairs) return;
+        const int t = idx / pairs, p = idx % pairs;
+        const float4 *col = reinterpret_cast<const float4 *>((mode ? b.buf0 : b.buf1) + 2 * p);
+        const size_t ld = (size_t)b.n2 / 2;
+        float4 *s = stg + (size_t)bsel * 16 * TH + tid;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            cp_async16(s + i * TH, col + (size_t)(512 * i + t) * ld);
+            cp_async16(s + (8 + i) * TH, col + (size_t)(512 * (i + 1) - t) * ld);
+        }
+    };
+    int bsel = 0;
+    if ((int)blockIdx.x < nw) issue(blockIdx.x, 0);
+    cp_async_commit();
+    for (int w = blockIdx.x; w < nw; w += gridDim.x, bsel ^= 1) {
+        cp_async_wait_all();
         FSP_UNIT(W, w, a, u);
         const int pairs = a.n2 / 2;
-        const int idx = u * 256 + (int)threadIdx.x;
-        if (idx >= 257 * pairs) continue;
+        const int idx = u * TH + tid;
+        const bool active = idx < 257 * pairs;
+        float4 R[8], M[8];   // rows 512 a + t and 512 b - t (b = a + 1)
+        const float4 *s = stg + (size_t)bsel * 16 * TH + tid;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            R[i] = s[i * TH];
+            M[i] = s[(8 + i) * TH];
+        }
+        // the other buffer was read in the previous iteration, whose stores used it
+        if (w + (int)gridDim.x < nw) issue(w + gridDim.x, bsel ^ 1);
+        cp_async_commit();
+        if (!active) continue;
         const int t = idx / pairs, p = idx % pairs;
         float2 *buf = mode ? a.buf0 : a.buf1;
         const bool want0 = mode ? a.out[0] != nullptr : true;   // the set written in place
         const bool want1 = mode && a.out[1] != nullptr;          // -i k0 set into buf1
-        const float4 *col = reinterpret_cast<const float4 *>(buf + 2 * p);
         const size_t ld = (size_t)a.n2 / 2;   // row stride in float4
-        float4 R[8], M[8];   // rows 512 a + t and 512 b - t (b = a + 1)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            R[i] = col[(size_t)(512 * i + t) * ld];
-            M[i] = col[(size_t)(512 * (i + 1) - t) * ld];
-        }
         const float2 *tw = a.tw0;   // the 8192-point table
         // one k2 = tt of the pair of offsets; sel 0: tt = t, 1: tt = 512 - t
         auto one = [&](int tt, int sel, bool withk, float2 *dst) {
@@ -300,7 +334,7 @@ __global__ void __launch_bounds__(256) p5_4s_a(const __grid_constant__ Work<MAXI
                 o[(size_t)(512 * n1 + tt) * ld] = make_float4(x[n1].x, x[n1].y, x[n1 + 8].x, x[n1 + 8].y);
         };
         const bool two = t != 0 && t != 256;
-        // every load is done above, so the in-place stores cannot overwrite an input
+        // every input of this unit is in registers, so the in-place stores cannot overwrite one
         if (want1) {
             one(t, 0, true, a.buf1);
             if (two) one(512 - t, 1, true, a.buf1);
@@ -310,6 +344,7 @@ __global__ void __launch_bounds__(256) p5_4s_a(const __grid_constant__ Work<MAXI
             if (two) one(512 - t, 1, false, buf);
         }
     }
+    cp_async_wait_all();
 }
 
 // Step 2.  Unit: (set, a < 8, tile of 16 columns); mode 0: one set, buf1 ->
